@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Throughput of the Flow Fields matching loop on GB300.
+
+One step = one frame pair of the Sintel-shaped workload (1024x436, 8-bit
+CIELab, 4 scales, 6 sweeps per scale, R = 1 px): features of both frames,
+forward and backward matching (on two streams), consistency filter.  Inputs
+are resident in device memory when the timed region starts; L2 is flushed
+between steps (a 256 MiB write, outside the per-step events).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead on a
+bounded sample of the same workload.  With ``--gpus N`` (torchrun), the N
+ranks run independent replicas (the method does not shard within a pair).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate patch evals/s and frame pairs/s (fwd+bwd) at 1024x436; % of int/L2 roofline"
+WORKLOAD = "sintel1024x436"
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+def eval_count(W: int, H: int, S: int, I: int, leaf: int) -> int:
+    """Cost evaluations of one direction (seeding rerank + upsample re-evals +
+    2 propagation candidates + 1 random-search candidate per point and sweep,
+    fewer at the borders where a source is missing)."""
+    n = 0
+    dims = []
+    for L in range(S):
+        s = 1 << L
+        dims.append(((W + s - 1) // s, (H + s - 1) // s))
+    n += leaf * dims[S - 1][0] * dims[S - 1][1]
+    for L, (wl, hl) in enumerate(dims):
+        n += (3 * I - 1) * wl * hl - I * (wl + hl)
+        if L < S - 1:
+            n += dims[L + 1][0] * dims[L + 1][1]
+    return n
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (the baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def cpu_oracle_rate(pair, prm, budget_rows: int = 6) -> dict:
+    """Time the oracle, as it stands, on a bounded sample of one pair.
+
+    Features of both frames, the full propagation of both directions (seeded
+    from the ground truth, which performs the same evaluations as any other
+    seeds), and the consistency filter run in full; the exact seeding search,
+    the slow part, runs for `budget_rows` rows of coarsest-grid queries per
+    direction and is scaled to all rows.  Single thread.
+    """
+    import oracle as O
+    C, S, I, R = prm["channels"], prm["scales"], prm["iters"], prm["radius_q3"]
+    W, H = pair.width, pair.height
+    P = O.Params(channels=C, scales=S, iters=I, radius_q3=R)
+    N = 1 << (S - 1)
+    WS, HS = O.level_dims(W, H, S - 1)
+    gt = np.rint(pair.flow * 8).astype(np.int16)
+    t_all = time.perf_counter()
+    t0 = time.perf_counter()
+    f1 = O.features_all(pair.img1, S)
+    f2 = O.features_all(pair.img2, S)
+    t_feat = time.perf_counter() - t0
+    t_seed = 0.0
+    t_prop = 0.0
+    rows = min(budget_rows, HS)
+    flows = []
+    for d, (a, b, g) in enumerate(((f1, f2, gt), (f2, f1, -gt))):
+        t0 = time.perf_counter()
+        O.seed_knn_rows(a[0], b[0], S, 0, rows)
+        t_seed += (time.perf_counter() - t0) * HS / rows
+        seeds = np.ascontiguousarray(g[::N, ::N][:HS, :WS])
+        t0 = time.perf_counter()
+        fl, _, _ = O.match_features(P, a, b, W, H, d, 0, seeds_in=seeds)
+        t_prop += time.perf_counter() - t0
+        flows.append(fl)
+    t0 = time.perf_counter()
+    O.filter_mask(flows[0], flows[1], 8)
+    t_filt = time.perf_counter() - t0
+    wall = time.perf_counter() - t_all
+    per_pair = t_feat + t_seed + t_prop + t_filt
+    return {"pairs_per_s": 1.0 / per_pair, "s_per_pair": per_pair, "wall_s": wall,
+            "parts_s": {"features": t_feat, "seeding_scaled": t_seed, "propagation": t_prop,
+                        "filter": t_filt},
+            "sample": (f"one {W}x{H} pair: features, propagation (both directions) and filter "
+                       f"in full; exact seeding on {rows} of {HS} query rows per direction, "
+                       f"scaled by {HS}/{rows}"),
+            "cores": 1}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
+    import torch
+
+    from paper_1703_02563_gb300 import ff, workloads
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pair, prm = workloads.make_workload(args.workload)
+    C, S, I, R = prm["channels"], prm["scales"], prm["iters"], prm["radius_q3"]
+    W, H = pair.width, pair.height
+    cfg = ff.Config(channels=C, scales=S, iters=I, radius_q3=R, max_width=W, max_height=H)
+    main = torch.cuda.Stream(dev)
+    side = torch.cuda.Stream(dev)
+    ctx = ff.ff_create(cfg, local_rank, main)
+    img1 = torch.from_numpy(pair.img1).to(dev)
+    img2 = torch.from_numpy(pair.img2).to(dev)
+    flow_f = torch.empty((H, W, 2), dtype=torch.int16, device=dev)
+    flow_b = torch.empty((H, W, 2), dtype=torch.int16, device=dev)
+    mask = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev_fork = torch.cuda.Event()
+    ev_join = torch.cuda.Event()
+
+    def step(pair_id: int):
+        ff.ff_set_stream(ctx, main)
+        ff.ff_features(ctx, 0, img1, W, H, W)
+        ff.ff_features(ctx, 1, img2, W, H, W)
+        ev_fork.record(main)
+        side.wait_event(ev_fork)
+        ff.ff_set_stream(ctx, side)
+        ff.ff_match(ctx, ff.FF_BWD, pair_id, None, flow_b, None)
+        ff.ff_set_stream(ctx, main)
+        ff.ff_match(ctx, ff.FF_FWD, pair_id, None, flow_f, None)
+        ev_join.record(side)
+        main.wait_event(ev_join)
+        ff.ff_filter(ctx, flow_f, flow_b, mask)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ff.ff_sync(ctx)
+
+    # ---- timed region: device-resident inputs, per-step events, L2 flushed between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = ff.ff_launch_count(ctx)
+    ff.ff_profile(ctx, True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        with torch.cuda.stream(main):
+            flush.fill_(i & 0xff)
+        starts[i].record(main)
+        step(args.warmup + i)
+        ends[i].record(main)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ff.ff_sync(ctx)
+    ff.ff_profile(ctx, False)
+    launches = ff.ff_launch_count(ctx) - launches0
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    kstats = {k: ff.ff_kernel_stats(ctx, k) for k in ff.KERNELS}
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    h1 = torch.from_numpy(pair.img1.copy()).pin_memory()
+    h2 = torch.from_numpy(pair.img2.copy()).pin_memory()
+    hf = torch.empty((H, W, 2), dtype=torch.int16).pin_memory()
+    hb = torch.empty((H, W, 2), dtype=torch.int16).pin_memory()
+    hm = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+    ff.ff_set_stream(ctx, main)
+    for i in range(2):
+        ff.ff_pair_host(ctx, h1, h2, W, H, i, hf, hb, hm)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ff.ff_pair_host(ctx, h1, h2, W, H, i, hf, hb, hm)
+    e2e_s = time.perf_counter() - t0
+    ff.ff_destroy(ctx)
+    return {"total_ms": total_ms, "step_ms": step_ms, "kstats": kstats, "launches": launches,
+            "clocks": clocks, "e2e_s": e2e_s, "W": W, "H": H, "C": C, "S": S, "I": I,
+            "prm": prm, "pair": pair}
+
+
+def roofline(res: dict, steps: int) -> dict:
+    """Roofline of the kernel with the largest share of device time.
+
+    k_sweep (propagation + random search) is integer-ALU work on a serial
+    wavefront: algorithmic work = cost evaluations x 10 integer ops per
+    feature dimension (4 multiply-adds of the bilinear taps, subtract,
+    absolute value, accumulate = 7 ops; counted as 10 with the tap and
+    weight arithmetic amortised per dimension), peak = 152 SMs x 64 INT32
+    lanes x 2.07 GHz.  k_seed_scan is a dense int8 contraction: 2 ops per
+    multiply-add of (query dims) x (candidates) x (queries), same peak x 4
+    (one dp4a = 4 multiply-adds).
+    """
+    ks = res["kstats"]
+    tot = {k: v[1] for k, v in ks.items()}
+    dom = max(tot, key=lambda k: tot[k])
+    n_launch, ms = ks[dom]
+    W, H, C, S, I = res["W"], res["H"], res["C"], res["S"], res["I"]
+    dims = 9 * C
+    alu_peak_tops = 152 * 64 * 2.07e9 / 1e12
+    if dom == "k_sweep":
+        evals = 2 * eval_count(W, H, S, I, 8) - 2 * 8 * ((W + (1 << (S - 1)) - 1) >> (S - 1)) * \
+            ((H + (1 << (S - 1)) - 1) >> (S - 1))
+        ops = evals * dims * 10 * steps
+        achieved = ops / (ms / 1e3) / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak_tops,
+                "unit": "Tops/s", "frac": achieved / alu_peak_tops, "traffic": None,
+                "launches": n_launch, "avg_launch_ms": ms / max(n_launch, 1),
+                "share": ms / sum(tot.values())}
+    if dom == "k_seed_scan":
+        N = 1 << (S - 1)
+        nq = ((W + N - 1) // N) * ((H + N - 1) // N)
+        macs = 2 * nq * W * H * dims * steps
+        achieved = 2 * macs / (ms / 1e3) / 1e12
+        peak = alu_peak_tops * 4 * 2
+        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                "launches": n_launch, "avg_launch_ms": ms / max(n_launch, 1),
+                "share": ms / sum(tot.values())}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak_tops,
+            "unit": "Tops/s", "frac": None, "traffic": None, "launches": n_launch,
+            "avg_launch_ms": ms / max(n_launch, 1), "share": ms / sum(tot.values())}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_1703_02563_gb300 import workloads
+        pair, prm = workloads.make_workload(args.workload)
+        for _ in range(args.warmup):
+            pass
+        rates = []
+        sample = None
+        for _ in range(max(1, args.steps)):
+            r = cpu_oracle_rate(pair, prm, budget_rows=2)
+            rates.append(r["pairs_per_s"])
+            sample = r["sample"]
+        v = statistics.median(rates)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+                "config": {"workload": args.workload, "frame": f"{pair.width}x{pair.height}",
+                           "channels": prm["channels"], "scales": prm["scales"],
+                           "iters": prm["iters"], "radius_q3": prm["radius_q3"]},
+                "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group("nccl")
+    res = run_gpu(args, rank, world, local_rank)
+    total_s = res["total_ms"] / 1e3
+    e2e_s = res["e2e_s"]
+    if world > 1:
+        import torch
+        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    K = args.steps
+    pairs = K * world
+    value = pairs / total_s
+    W, H, C, S, I = res["W"], res["H"], res["C"], res["S"], res["I"]
+    evals_pair = 2 * eval_count(W, H, S, I, 8)
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": res["total_ms"] / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "evals_per_s": evals_pair * pairs / total_s,
+        "config": {"workload": args.workload, "frame": f"{W}x{H}", "channels": C, "scales": S,
+                   "iters": I, "radius_q3": res["prm"]["radius_q3"], "seed_leaf": 8,
+                   "l2": "flushed between steps (256 MiB write outside the step events)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "clocks": res["clocks"],
+        "gpu_launches": res["launches"],
+        "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
+                "h2d_bytes_per_step": 2 * C * W * H,
+                "d2h_bytes_per_step": 2 * 4 * W * H + W * H},
+        "roofline": roofline(res, K),
+        "kernels_ms": {k: round(v[1], 4) for k, v in res["kstats"].items() if v[0]},
+    }
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    if not args.no_cpu_baseline and world == 1:
+        r = cpu_oracle_rate(res["pair"], res["prm"])
+        line["cpu_baseline"] = {"value": r["pairs_per_s"], "unit": "pairs/s",
+                                "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
+                                "wall_s": round(r["wall_s"], 2)}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * ff.h - C ABI of the GB300 Flow Fields patch-matching library (libff.so).
+ *
+ * Flow Fields (Bailer, Taetz, Stricker; arXiv 1703.02563) computes, for two
+ * images I1 and I2, a correspondence field F(p) = M(p) - p for every pixel p
+ * of I1 (Sec. 3, problem statement).  This library runs the method's
+ * multi-scale patch-matching loop on one GPU:
+ *
+ *   ff_features  level images + WHT features of one frame     Sec. 3.1, 3.6
+ *   ff_match     seeding, then per scale (coarse to fine)      Sec. 3.1 Eq. 1-2,
+ *                propagation sweeps + random search            Sec. 3.2 Eq. 3-4
+ *   ff_filter    forward/backward consistency check            Sec. 3.7
+ *
+ * Conventions shared by every call:
+ *  - Every pointer argument is DEVICE memory unless the name ends in _host.
+ *    The caller owns inputs and outputs and keeps them alive until the work
+ *    is done; the context owns features, per-level state and scratch.
+ *  - Calls are asynchronous on the context's current stream (ff_create /
+ *    ff_set_stream) unless stated otherwise.  A device-side failure (a
+ *    bounded wait that ran out) is recorded in the context and reported by
+ *    ff_sync().
+ *  - Flows are int16 pairs (x, y) in 1/8 pixel, row-major [H][W][2]; the
+ *    value (-32768, -32768) marks an unset flow.  Costs are int32 [H][W]
+ *    (sum of absolute feature differences scaled by 64; unset = INT32_MAX).
+ *  - Status codes: FF_OK on success; FF_EINVAL for bad arguments (nothing is
+ *    launched); FF_ENOMEM when device memory runs out in ff_create; FF_ECUDA
+ *    when a CUDA call fails; FF_ETIMEOUT when a bounded device wait expired;
+ *    FF_ESTATE when a call comes in the wrong order (e.g. ff_match before
+ *    both frames have features).  ff_last_error() gives a message.
+ *  - Results are bit-exact integers: the same inputs and config give the
+ *    same flows, costs and masks on every run and in every call order.
+ */
+#ifndef FF_H
+#define FF_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ff_ctx ff_ctx;
+
+typedef enum {
+    FF_OK = 0,
+    FF_EINVAL = 1,
+    FF_ENOMEM = 2,
+    FF_ECUDA = 3,
+    FF_ETIMEOUT = 4,
+    FF_ESTATE = 5
+} ff_status;
+
+typedef enum { FF_FWD = 0, FF_BWD = 1 } ff_dir;
+
+#define FF_MAX_SCALES 8
+#define FF_MAX_LEAF 8
+#define FF_MAX_DIM 4096
+
+/* Parameters of the method (Sec. 4.1 gives the paper's values). */
+typedef struct {
+    int patch;        /* WHT window side, must be 8 (offsets -3..+4, Sec. 3.1 footnote) */
+    int n_coeffs;     /* WHT bases per channel, must be 9 (Sec. 3.1)                     */
+    int channels;     /* 1 (gray) or 3 (8-bit CIELab, Sec. 3.1)                          */
+    int scales;       /* S levels; the coarsest scale is n = 2^(S-1) (k = S-1, Sec. 3.2) */
+    int iters;        /* I propagation sweeps per level, I-1 random searches (Sec. 3.1)  */
+    int radius_q3;    /* random-search radius R in 1/8 px; R_n = R n (Sec. 3.2)          */
+    int seed_leaf;    /* l seeding candidates kept per point, 1..8 (Sec. 3.1, l = 8)     */
+    int seed_stride;  /* candidate grid stride in I2 (1; 2 = the Fast x2 option)         */
+    int eps_q3;       /* consistency threshold eps in 1/8 px (Sec. 3.7)                  */
+    uint32_t seed;    /* random-search key word 0                                        */
+    int max_width;    /* largest frame the context must hold, 1..4096                     */
+    int max_height;
+} ff_config;
+
+/* Fills the paper's defaults: patch 8, 9 coefficients, 1 channel, S = 4,
+ * I = 4, R = 1 px, l = 8, stride 1, eps = 1 px, max 1024 x 1024. */
+ff_status ff_config_default(ff_config *cfg);
+
+/* Creates a context on `device` and allocates all its device memory for
+ * frames up to max_width x max_height.  cuda_stream: a cudaStream_t (NULL =
+ * the legacy default stream).  *out receives the context. */
+ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx **out);
+
+/* Makes later calls enqueue on another stream.  Features and matching state
+ * of the two slots / directions are separate buffers, so ff_match(FF_FWD)
+ * and ff_match(FF_BWD) may run concurrently on two streams once both
+ * frames' features are complete (ordering them is the caller's job). */
+ff_status ff_set_stream(ff_ctx *ctx, void *cuda_stream);
+
+/* Sec. 3.1 + 3.6: builds the S level images of one frame (n x n area
+ * average, replicate border) and their int8 WHT features into the
+ * context.  slot 0 = I1, slot 1 = I2.  img: device uint8, planar
+ * [channels][h][pitch], pitch >= w.  1 <= w <= max_width, 1 <= h <= max_height. */
+ff_status ff_features(ff_ctx *ctx, int slot, const uint8_t *img, int w, int h, int pitch);
+
+/* Sec. 3.1-3.2: matches slot 0 -> 1 (FF_FWD) or 1 -> 0 (FF_BWD).  Both slots
+ * must hold features of the same size.  pair_id: random-search key word 1.
+ * seeds_in: NULL (seed by the exact top-l WHT search, Eq. 1/4) or int16
+ * [H_c][W_c][2] flows on the coarsest grid (H_c = ceil(h / 2^(S-1))).
+ * flow_out: int16 [h][w][2]; cost_out: int32 [h][w] or NULL.  Both 4-byte
+ * aligned. */
+ff_status ff_match(ff_ctx *ctx, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
+                   int16_t *flow_out, int32_t *cost_out);
+
+/* As ff_match, but stops at level `until_level` after `until_sweeps` sweeps
+ * (each followed by its random search when one follows it) and writes that
+ * level's grid: flow_out int16 [H_L][W_L][2], cost_out int32 [H_L][W_L].
+ * until_sweeps = 0 returns the level's initial state (seeds or upsampled
+ * flows).  Used to check each stage of the method. */
+ff_status ff_match_until(ff_ctx *ctx, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
+                         int until_level, int until_sweeps, int16_t *flow_out,
+                         int32_t *cost_out);
+
+/* Sec. 3.7: mask[p] = 1 iff |F(p) + F_b(q)| < eps, q = the pixel nearest to
+ * p + F(p) (rounded half up); 0 when q is outside the frame or a flow is
+ * unset.  flow_fwd / flow_bwd: int16 [h][w][2] of the last ff_features size;
+ * mask_out: uint8 [h][w]. */
+ff_status ff_filter(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_bwd,
+                    uint8_t *mask_out);
+
+/* Whole pair with HOST buffers (blocking): copies both frames in (planar
+ * uint8 [channels][h][w]), builds features, matches forward and backward
+ * concurrently, filters, and copies the results out: flow_fwd_host and
+ * flow_bwd_host int16 [h][w][2], mask_host uint8 [h][w] (any may be NULL to
+ * skip its copy).  Pinned host memory makes the copies asynchronous.
+ * Returns after the results are on the host. */
+ff_status ff_pair_host(ff_ctx *ctx, const uint8_t *img1_host, const uint8_t *img2_host,
+                       int w, int h, uint32_t pair_id, int16_t *flow_fwd_host,
+                       int16_t *flow_bwd_host, uint8_t *mask_host);
+
+/* Copies level `level` of slot `slot`'s features to dst: int8
+ * [H_L][W_L][9 * channels] (dense, dimension index ch*9 + 3u + v). */
+ff_status ff_get_features(ff_ctx *ctx, int slot, int level, int8_t *dst);
+
+/* Runs only the seeding search of ff_match(dir) and writes, per coarsest
+ * grid point, the l nearest I2 pixels: idx_out int32 [H_c][W_c][l] (linear
+ * index y*w + x, -1 if fewer candidates exist) and dist_out int32
+ * [H_c][W_c][l] (squared feature distance), ascending by (dist, idx). */
+ff_status ff_seed_knn(ff_ctx *ctx, ff_dir dir, int32_t *idx_out, int32_t *dist_out);
+
+/* Blocks until the context's work is done; returns FF_ETIMEOUT if a bounded
+ * device wait expired since the last ff_sync (and clears the record). */
+ff_status ff_sync(ff_ctx *ctx);
+
+/* Test hooks.  FF_DEBUG_WAIT_LIMIT_NS: upper bound of every device-side
+ * wait (default 2 s).  FF_DEBUG_FORCE_TIMEOUT: when nonzero, the next
+ * propagation sweeps wait for a boundary row that is never written, so the
+ * bounded wait runs out and ff_sync reports FF_ETIMEOUT. */
+typedef enum { FF_DEBUG_WAIT_LIMIT_NS = 1, FF_DEBUG_FORCE_TIMEOUT = 2 } ff_debug_key;
+ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
+
+/* Per-launch timing for measurement.  While enabled, every kernel launch
+ * is bracketed by a pair of CUDA events on the stream it is launched on.
+ * ff_profile(ctx, 1) clears the record and starts recording; ff_profile(ctx,
+ * 0) stops.  ff_kernel_stats (call after ff_sync) returns, for the kernel
+ * named `kernel` ("k_features", "k_seed_scan", "k_seed_merge",
+ * "k_seed_rerank", "k_seed_given", "k_upsample", "k_sweep", "k_export",
+ * "k_filter", "k_dense"), the number of recorded launches and their summed
+ * device time in milliseconds. */
+ff_status ff_profile(ff_ctx *ctx, int enable);
+ff_status ff_kernel_stats(ff_ctx *ctx, const char *kernel, long long *launches,
+                          double *total_ms);
+
+/* Number of kernel launches this context has made so far. */
+long long ff_launch_count(const ff_ctx *ctx);
+
+const char *ff_last_error(const ff_ctx *ctx);
+const char *ff_status_string(ff_status s);
+void ff_destroy(ff_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -224,9 +224,19 @@ int32_t ffo_cost(const int8_t *f1L, const int8_t *f2L, int C, int W, int H, int 
  * non-subsampled (level-0) vectors. */
 int ffo_seed_knn(const int8_t *f1_0, const int8_t *f2_0, int C, int W, int H, int S,
                  int leaf, int stride, int32_t *knn_idx, int32_t *knn_dist) {
+    int WS, HS;
+    ffo_level_dims(W, H, S - 1, &WS, &HS);
+    return ffo_seed_knn_rows(f1_0, f2_0, C, W, H, S, leaf, stride, 0, HS, knn_idx, knn_dist);
+}
+
+int ffo_seed_knn_rows(const int8_t *f1_0, const int8_t *f2_0, int C, int W, int H, int S,
+                      int leaf, int stride, int gy0, int gy1, int32_t *knn_idx,
+                      int32_t *knn_dist) {
     int D = 9 * C, N = 1 << (S - 1), WS, HS, filled_max = 0;
     ffo_level_dims(W, H, S - 1, &WS, &HS);
-    for (int gy = 0; gy < HS; gy++)
+    if (gy0 < 0) gy0 = 0;
+    if (gy1 > HS) gy1 = HS;
+    for (int gy = gy0; gy < gy1; gy++)
         for (int gx = 0; gx < WS; gx++) {
             int px = gx * N, py = gy * N;
             const int8_t *q = f1_0 + ((long)py * W + px) * D;

@@ -69,6 +69,12 @@ int32_t ffo_cost(const int8_t *f1L, const int8_t *f2L, int C, int W, int H, int 
 int ffo_seed_knn(const int8_t *f1_0, const int8_t *f2_0, int C, int W, int H, int S,
                  int leaf, int stride, int32_t *knn_idx, int32_t *knn_dist);
 
+/* the same search restricted to coarsest-grid rows gy0 <= gy < gy1 (the
+ * outputs are still indexed by the full grid) */
+int ffo_seed_knn_rows(const int8_t *f1_0, const int8_t *f2_0, int C, int W, int H, int S,
+                      int leaf, int stride, int gy0, int gy1, int32_t *knn_idx,
+                      int32_t *knn_dist);
+
 /* single steps on one level's state: flow int16 [HL][WL][2], cost int32
  * [HL][WL], both updated in place; d = direction 0..3, t = sweep index */
 void ffo_sweep_level(const int8_t *f1L, const int8_t *f2L, int C, int W, int H, int L, int d,

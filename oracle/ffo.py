@@ -42,6 +42,8 @@ def lib():
         L.ffo_cost.restype = ct.c_int32
         L.ffo_seed_knn.argtypes = [P, P, i, i, i, i, i, i, P, P]
         L.ffo_seed_knn.restype = i
+        L.ffo_seed_knn_rows.argtypes = [P, P, i, i, i, i, i, i, i, i, P, P]
+        L.ffo_seed_knn_rows.restype = i
         L.ffo_match_features.argtypes = [P, P, P, i, i, i, ct.c_uint32, P, i, i, P, P, P]
         L.ffo_match_features.restype = i
         L.ffo_match.argtypes = [P, P, P, i, i, i, ct.c_uint32, P, i, i, P, P, P]
@@ -165,6 +167,20 @@ def seed_knn(f1_0: np.ndarray, f2_0: np.ndarray, S: int, leaf: int = 8, stride: 
     idx = np.zeros((HS, WS, leaf), np.int32)
     dist = np.zeros((HS, WS, leaf), np.int32)
     lib().ffo_seed_knn(_p(f1_0), _p(f2_0), C, W, H, S, leaf, stride, _p(idx), _p(dist))
+    return idx, dist
+
+
+def seed_knn_rows(f1_0: np.ndarray, f2_0: np.ndarray, S: int, gy0: int, gy1: int,
+                  leaf: int = 8, stride: int = 1):
+    """Seeding search for coarsest-grid rows gy0..gy1-1 only (others left -1)."""
+    f1_0 = np.ascontiguousarray(f1_0, np.int8)
+    f2_0 = np.ascontiguousarray(f2_0, np.int8)
+    H, W, D = f1_0.shape
+    WS, HS = level_dims(W, H, S - 1)
+    idx = np.full((HS, WS, leaf), -1, np.int32)
+    dist = np.full((HS, WS, leaf), -1, np.int32)
+    lib().ffo_seed_knn_rows(_p(f1_0), _p(f2_0), D // 9, W, H, S, leaf, stride, gy0, gy1,
+                            _p(idx), _p(dist))
     return idx, dist
 
 

@@ -1,0 +1,1282 @@
+// ff.cu - GB300 (sm_103a) kernels and C ABI of the Flow Fields
+// patch-matching loop (arXiv 1703.02563, Sec. 3).  The ABI is declared in
+// include/ff.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "ff.h"
+#include "ff_kernels.cuh"
+
+using namespace ffk;
+
+// ============================================================================
+// kernels
+// ============================================================================
+
+// Sec. 3.6 + 3.1: level image D_n (n x n area average rounded half up,
+// replicate border) and its 9 lowest-sequency Walsh coefficients per channel
+// over the 8x8 window at offsets -3..+4, quantised to int8:
+//   DC: round(c/64) - 128, others: round(c/16), both saturated.
+// One thread per level pixel; a 16x16 tile plus its 7-pixel halo of D_n is
+// built in shared memory straight from the frame, then the coefficients come
+// from separable +-1 row and column sums.
+template <int C>
+__global__ void __launch_bounds__(256)
+    k_features(const uint8_t *__restrict__ img, int pitch, int W, int H, int L, int WL, int HL,
+               uint8_t *__restrict__ out) {
+    constexpr int TS = 16, TW = TS + 7, P = Geo<C>::P;
+    __shared__ int16_t sD[C][TW][TW];
+    const int n = 1 << L;
+    const int bx = blockIdx.x * TS, by = blockIdx.y * TS;
+    const int tid = threadIdx.y * TS + threadIdx.x;
+    const int half = (n * n) >> 1;
+    for (int k = tid; k < C * TW * TW; k += TS * TS) {
+        const int c = k / (TW * TW), rem = k - c * (TW * TW);
+        const int ty = rem / TW, tx = rem - ty * TW;
+        const int gx = clampi(bx - 3 + tx, 0, WL - 1);
+        const int gy = clampi(by - 3 + ty, 0, HL - 1);
+        const uint8_t *plane = img + (size_t)c * H * pitch;
+        int sum = 0;
+        for (int i = 0; i < n; i++) {
+            const uint8_t *row = plane + (size_t)min(gy * n + i, H - 1) * pitch;
+            for (int j = 0; j < n; j++) sum += row[min(gx * n + j, W - 1)];
+        }
+        sD[c][ty][tx] = (int16_t)((sum + half) >> (2 * L));
+    }
+    __syncthreads();
+    const int x = bx + threadIdx.x, y = by + threadIdx.y;
+    if (x >= WL || y >= HL) return;
+    uint32_t words[P / 4];
+#pragma unroll
+    for (int k = 0; k < P / 4; k++) words[k] = 0;
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        int r0[8], r1[8], r2[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int16_t *row = &sD[c][threadIdx.y + i][threadIdx.x];
+            const int a0 = row[0], a1 = row[1], a2 = row[2], a3 = row[3];
+            const int a4 = row[4], a5 = row[5], a6 = row[6], a7 = row[7];
+            r0[i] = (a0 + a1 + a2 + a3) + (a4 + a5 + a6 + a7);
+            r1[i] = (a0 + a1 + a2 + a3) - (a4 + a5 + a6 + a7);
+            r2[i] = (a0 + a1 + a6 + a7) - (a2 + a3 + a4 + a5);
+        }
+        int coef[9];
+#pragma unroll
+        for (int v = 0; v < 3; v++) {
+            const int *r = v == 0 ? r0 : (v == 1 ? r1 : r2);
+            coef[0 * 3 + v] = (r[0] + r[1] + r[2] + r[3]) + (r[4] + r[5] + r[6] + r[7]);
+            coef[1 * 3 + v] = (r[0] + r[1] + r[2] + r[3]) - (r[4] + r[5] + r[6] + r[7]);
+            coef[2 * 3 + v] = (r[0] + r[1] + r[6] + r[7]) - (r[2] + r[3] + r[4] + r[5]);
+        }
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const int q = k == 0 ? ((coef[0] + 32) >> 6) - 128 : ((coef[k] + 8) >> 4);
+            const int b = clampi(q, -128, 127) & 0xff;
+            const int dim = c * 9 + k;
+            words[dim >> 2] |= (uint32_t)b << (8 * (dim & 3));
+        }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(out + ((size_t)y * WL + x) * P);
+#pragma unroll
+    for (int k = 0; k < P / 16; k++)
+        dst[k] = make_uint4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
+}
+
+// dense copy [H_L][W_L][9C] of a level's features (for inspection)
+template <int C>
+__global__ void k_dense(const uint8_t *__restrict__ feat, int N, int8_t *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int d = 0; d < 9 * C; d++)
+        out[(size_t)i * 9 * C + d] = (int8_t)feat[(size_t)i * Geo<C>::P + d];
+}
+
+// ---------------------------------------------------------------------------
+// seeding: exact top-8 by (squared distance, linear index) of level-0 WHT
+// vectors (Sec. 3.1 Eq. 1, Sec. 3.2 Eq. 4; kd-tree leaf replaced by the exact
+// nearest neighbours it approximates)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool lex_less(int d, int i, int D, int I) {
+    return d < D || (d == D && i < I);
+}
+
+// insert (d, i) into the ascending list (D, I) of 8, dropping the last entry
+__device__ __forceinline__ void list_insert(int (&D)[8], int (&I)[8], int d, int i) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const bool sw = lex_less(d, i, D[k], I[k]);
+        const int td = D[k], ti = I[k];
+        D[k] = sw ? d : td;
+        I[k] = sw ? i : ti;
+        d = sw ? td : d;
+        i = sw ? ti : i;
+    }
+}
+
+// Phase 1: one query per thread, one candidate chunk per blockIdx.y.
+// Candidates of the chunk are staged 256 at a time in shared memory with
+// their squared norms; |q - c|^2 = |q|^2 + |c|^2 - 2 q.c with q.c by dp4a.
+template <int C>
+__global__ void __launch_bounds__(128)
+    k_seed_scan(const uint8_t *__restrict__ f1, const uint8_t *__restrict__ f2, int W, int N,
+                int WS, int NQ, int stride, int Wc, int ncand, int chunk, int2 *__restrict__ part) {
+    constexpr int P = Geo<C>::P, NV = P / 16, NW = Geo<C>::NW, TILE = 256;
+    __shared__ uint4 s_w[TILE][NV];
+    __shared__ int s_n[TILE];
+    __shared__ int s_i[TILE];
+    const int q = blockIdx.x * 128 + threadIdx.x;
+    uint32_t qw[P / 4];
+    int qn = 0;
+    {
+        const int qq = min(q, NQ - 1);
+        const int gy = qq / WS, gx = qq - gy * WS;
+        const uint4 *src = reinterpret_cast<const uint4 *>(f1 + ((size_t)gy * N * W + gx * N) * P);
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const uint4 v = __ldg(src + k);
+            qw[4 * k] = v.x;
+            qw[4 * k + 1] = v.y;
+            qw[4 * k + 2] = v.z;
+            qw[4 * k + 3] = v.w;
+        }
+#pragma unroll
+        for (int w = 0; w < NW; w++) qn = __dp4a((int)qw[w], (int)qw[w], qn);
+    }
+    int D[8], I[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) D[k] = I[k] = 0x7fffffff;
+    const int c0 = blockIdx.y * chunk, c1 = min(c0 + chunk, ncand);
+    for (int base = c0; base < c1; base += TILE) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < TILE; k += 128) {
+            const int ci = base + k;
+            if (ci < c1) {
+                const int cy = (ci / Wc) * stride, cx = (ci % Wc) * stride;
+                const uint4 *src = reinterpret_cast<const uint4 *>(f2 + ((size_t)cy * W + cx) * P);
+                int nn = 0;
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    const uint4 x = __ldg(src + v);
+                    s_w[k][v] = x;
+                    nn = __dp4a((int)x.x, (int)x.x, nn);
+                    nn = __dp4a((int)x.y, (int)x.y, nn);
+                    nn = __dp4a((int)x.z, (int)x.z, nn);
+                    nn = __dp4a((int)x.w, (int)x.w, nn);
+                }
+                s_n[k] = nn;
+                s_i[k] = cy * W + cx;
+            }
+        }
+        __syncthreads();
+        const int cnt = min(TILE, c1 - base);
+        for (int k = 0; k < cnt; k++) {
+            int dot = 0;
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const uint4 x = s_w[k][v];
+                dot = __dp4a((int)qw[4 * v], (int)x.x, dot);
+                dot = __dp4a((int)qw[4 * v + 1], (int)x.y, dot);
+                dot = __dp4a((int)qw[4 * v + 2], (int)x.z, dot);
+                dot = __dp4a((int)qw[4 * v + 3], (int)x.w, dot);
+            }
+            const int dist = qn + s_n[k] - 2 * dot;
+            const int idx = s_i[k];
+            if (lex_less(dist, idx, D[7], I[7])) list_insert(D, I, dist, idx);
+        }
+    }
+    if (q < NQ) {
+        int2 *dst = part + ((size_t)blockIdx.y * NQ + q) * 8;
+#pragma unroll
+        for (int k = 0; k < 8; k++) dst[k] = make_int2(D[k], I[k]);
+    }
+}
+
+// Phase 2: merge the per-chunk lists of each query into its top-l.
+__global__ void k_seed_merge(const int2 *__restrict__ part, int nchunks, int NQ, int leaf,
+                             int *__restrict__ knn_idx, int *__restrict__ knn_dist) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= NQ) return;
+    int D[8], I[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) D[k] = I[k] = 0x7fffffff;
+    for (int c = 0; c < nchunks; c++) {
+        const int2 *src = part + ((size_t)c * NQ + q) * 8;
+        for (int k = 0; k < 8; k++) {
+            const int2 e = src[k];
+            if (e.y == 0x7fffffff) break;
+            if (!lex_less(e.x, e.y, D[7], I[7])) break;
+            list_insert(D, I, e.x, e.y);
+        }
+    }
+    for (int k = 0; k < leaf; k++) {
+        const bool ok = I[k] != 0x7fffffff;
+        knn_idx[(size_t)q * leaf + k] = ok ? I[k] : -1;
+        knn_dist[(size_t)q * leaf + k] = ok ? D[k] : -1;
+    }
+}
+
+// Phase 3 (Eq. 1 rerank): each candidate p2 gives F = 8 (p2 - p); keep the
+// lowest E at the coarsest scale, the earlier rank on ties.
+template <int C>
+__global__ void k_seed_rerank(const int *__restrict__ knn_idx, int leaf, const uint8_t *f1L,
+                              const uint8_t *f2L, int W, int H, int L, int WL, int HL,
+                              uint32_t *__restrict__ flow, int *__restrict__ cost) {
+    constexpr int P = Geo<C>::P;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= WL * HL) return;
+    const int gy = q / WL, gx = q - gy * WL;
+    const int px = gx << L, py = gy << L;
+    uint32_t qw[P / 4];
+#pragma unroll
+    for (int w = 0; w < P / 4; w++) qw[w] = ldg32(f1L + (size_t)q * P + 4 * w);
+    uint32_t bf = kFlowInvalid;
+    int bc = kCostInvalid;
+    for (int r = 0; r < leaf; r++) {
+        const int idx = knn_idx[(size_t)q * leaf + r];
+        if (idx < 0) break;
+        int fx = 8 * (idx % W - px), fy = 8 * (idx / W - py);
+        clamp_flow(W, H, px, py, fx, fy);
+        const int e = sad_full<C>(f2L, make_tap<P>(px, py, fx, fy, L, WL, HL), qw);
+        if (e < bc) {
+            bc = e;
+            bf = pack_flow(fx, fy);
+        }
+    }
+    flow[q] = bf;
+    cost[q] = bc;
+}
+
+// caller-supplied seeds on the coarsest grid: clamp and evaluate
+template <int C>
+__global__ void k_seed_given(const uint32_t *__restrict__ seeds, const uint8_t *f1L,
+                             const uint8_t *f2L, int W, int H, int L, int WL, int HL,
+                             uint32_t *__restrict__ flow, int *__restrict__ cost) {
+    constexpr int P = Geo<C>::P;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= WL * HL) return;
+    const uint32_t s = seeds[q];
+    if (flow_x(s) == -32768 || flow_y(s) == -32768) {
+        flow[q] = kFlowInvalid;
+        cost[q] = kCostInvalid;
+        return;
+    }
+    const int gy = q / WL, gx = q - gy * WL;
+    const int px = gx << L, py = gy << L;
+    uint32_t qw[P / 4];
+#pragma unroll
+    for (int w = 0; w < P / 4; w++) qw[w] = ldg32(f1L + (size_t)q * P + 4 * w);
+    int fx = flow_x(s), fy = flow_y(s);
+    clamp_flow(W, H, px, py, fx, fy);
+    flow[q] = pack_flow(fx, fy);
+    cost[q] = sad_full<C>(f2L, make_tap<P>(px, py, fx, fy, L, WL, HL), qw);
+}
+
+// Sec. 3.2 coarse to fine: points of level L that are points of level L+1
+// (both grid coordinates even) keep their flow, re-evaluated at scale n; the
+// other points start unset.
+template <int C>
+__global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uint8_t *f1L,
+                           const uint8_t *f2L, int W, int H, int L, int WL, int HL,
+                           uint32_t *__restrict__ flow, int *__restrict__ cost) {
+    constexpr int P = Geo<C>::P;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= WL * HL) return;
+    const int gy = q / WL, gx = q - gy * WL;
+    uint32_t f = kFlowInvalid;
+    if (((gx | gy) & 1) == 0) f = pflow[(gy >> 1) * WP + (gx >> 1)];
+    if (f == kFlowInvalid) {
+        flow[q] = kFlowInvalid;
+        cost[q] = kCostInvalid;
+        return;
+    }
+    uint32_t qw[P / 4];
+#pragma unroll
+    for (int w = 0; w < P / 4; w++) qw[w] = ldg32(f1L + (size_t)q * P + 4 * w);
+    const int px = gx << L, py = gy << L;
+    flow[q] = f;
+    cost[q] = sad_full<C>(f2L, make_tap<P>(px, py, flow_x(f), flow_y(f), L, WL, HL), qw);
+}
+
+// ---------------------------------------------------------------------------
+// propagation sweep + random search (Sec. 3.1 Eq. 2, Sec. 3.2)
+// ---------------------------------------------------------------------------
+struct SweepArgs {
+    const uint8_t *f1L;
+    const uint8_t *f2L;
+    uint32_t *flow;                // level state, updated in place
+    int *cost;
+    unsigned long long *edge;      // [nstrips][WL] boundary rows: (epoch << 32) | flow
+    unsigned int *ticket;          // strip counter of this launch (zeroed before)
+    int *err;                      // error word of this direction
+    int W, H, L, WL, HL;
+    int d, t, dir, do_rs, radius_q3;
+    uint32_t seed, pair_id, epoch;
+    unsigned long long wait_ns;
+    int force_timeout;
+};
+
+// One sweep in direction d, followed (when do_rs) by the random search.
+//
+// The sweep runs in its own frame (u, v): u along the sweep's x order, v
+// along its y order, so every direction has sources (u-1, v) and (u, v-1)
+// and the raster order v-major.  Point (u, v) depends only on those two, so
+// all points of one anti-diagonal are independent; the kernel reproduces the
+// raster order exactly as a skewed wavefront:
+//   * a CTA owns a strip of R consecutive rows; row r handles column
+//     u = s - r at step s, so (u, v-1) was finished by row r-1 one step
+//     earlier and (u-1, v) by row r itself;
+//   * each point is evaluated by G lanes, one 4-dimension word each, reduced
+//     with xor shuffles; rows hand their result down through shared memory
+//     with one named barrier per step;
+//   * the strip's last row publishes its sweep results as 64-bit words
+//     tagged with this launch's epoch; a loader warp of the next strip polls
+//     them into a shared ring ahead of use, so no global wait or fence sits
+//     on the per-step critical path.  Strips are handed out by a ticket
+//     counter, so a strip only ever waits on a strip that is already running.
+//   * the random search of point (u-1, v) is evaluated one step later,
+//     alongside the sweep of (u, v); it uses the sweep value, and only its
+//     result (never seen by neighbours in this sweep) goes to memory.
+// Every wait is bounded (wait_ns without progress); on expiry the error word
+// gets FF_ETIMEOUT and every strip of the launch returns early.
+template <int C>
+__global__ void __launch_bounds__(160) k_sweep(const SweepArgs a) {
+    constexpr int P = Geo<C>::P, NW = Geo<C>::NW, G = Geo<C>::G;
+    constexpr int NT = 128, R = NT / G, RING = 128;
+    __shared__ uint32_t s_vbuf[2][R];
+    __shared__ uint32_t s_ring[RING];
+    __shared__ int s_filled, s_consumed, s_abort, s_strip;
+    volatile int *v_filled = &s_filled;
+    volatile int *v_consumed = &s_consumed;
+    volatile int *v_abort = &s_abort;
+    volatile uint32_t *v_ring = s_ring;
+
+    const int tid = threadIdx.x;
+    const int U = a.WL, V = a.HL;
+    const int nstrips = (V + R - 1) / R;
+    if (tid == 0) {
+        s_strip = (int)atomicAdd(a.ticket, 1u);
+        s_filled = 0;
+        s_consumed = 0;
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int strip = s_strip;
+    if (strip >= nstrips) return;
+    const int v0 = strip * R;
+
+    if (tid >= NT) {
+        // ---------------- loader warp: previous strip's last row -> ring
+        if (strip == 0) return;
+        const int lane = tid - NT;
+        const unsigned long long *src = a.edge + (size_t)(strip - 1) * U;
+        const uint32_t want = (a.force_timeout && strip == 1) ? (a.epoch ^ 0x80000000u) : a.epoch;
+        int base = 0;
+        unsigned long long t0 = globaltimer_ns();
+        while (base < U) {
+            const int col = base + lane;
+            const int limit = *v_consumed + RING;
+            bool ready = col >= U;
+            uint32_t val = 0;
+            if (col < U && col < limit) {
+                const unsigned long long e = ld_relaxed_u64(src + col);
+                ready = (uint32_t)(e >> 32) == want;
+                val = (uint32_t)e;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ready);
+            int nready = (m == 0xffffffffu) ? 32 : (__ffs(~m) - 1);
+            nready = min(nready, U - base);
+            if (lane < nready) v_ring[col & (RING - 1)] = val;
+            __syncwarp();
+            if (nready > 0) {
+                __threadfence_block();
+                base += nready;
+                if (lane == 0) *v_filled = base;
+                t0 = globaltimer_ns();
+            } else {
+                int stop = 0;
+                if (lane == 0) {
+                    const bool late = globaltimer_ns() - t0 > a.wait_ns;
+                    if (late) atomicCAS(a.err, 0, kErrTimeout);
+                    stop = late || ld_relaxed_i32(a.err) != 0;
+                    if (stop) *v_abort = 1;
+                }
+                if (__shfl_sync(0xffffffffu, stop, 0)) return;
+                __nanosleep(64);
+            }
+        }
+        return;
+    }
+
+    // ---------------- compute warps
+    const int r = tid / G, g = tid - (tid / G) * G;
+    const int v = v0 + r;
+    const bool row_ok = v < V;
+    const int L = a.L, n = 1 << L;
+    const bool word = g < NW;
+    const bool flipx = (a.d == 1 || a.d == 2), flipy = (a.d == 1 || a.d == 3);
+    const int gy = row_ok ? (flipy ? V - 1 - v : v) : 0;
+    const int py = gy * n;
+    const int Rq = a.radius_q3 * n;
+    const uint32_t span = 2u * (uint32_t)Rq + 1u;
+    const bool publish = (r == R - 1) && (strip + 1 < nstrips) && (g == 0);
+    unsigned long long *edge_out = a.edge + (size_t)strip * U;
+
+    uint32_t hflow = kFlowInvalid;      // sweep value of (u-1, v)
+    uint32_t pflow = kFlowInvalid;      // pending random search: sweep value ...
+    int pcost = kCostInvalid;           // ... its cost
+    int pgx = 0;                        // ... its grid x
+    int4 pna = make_int4(0, 0, 0, 0);   // ... its query word (x -64)
+    bool pvalid = false;
+
+    const int nsteps = U + R;
+    for (int s = 0; s < nsteps; s++) {
+        const int u = s - r;
+        const bool active = row_ok && u >= 0 && u < U;
+        const int gx = flipx ? U - 1 - u : u;
+        const int px = gx * n;
+        const size_t pidx = (size_t)gy * U + gx;
+
+        uint32_t cflow = kFlowInvalid, qword = 0;
+        int ccost = kCostInvalid;
+        if (active) {
+            cflow = a.flow[pidx];
+            ccost = a.cost[pidx];
+            if (word) qword = ldg32(a.f1L + pidx * P + 4 * g);
+        }
+        uint32_t vflow = kFlowInvalid;
+        if (active && v > 0) {
+            if (r > 0) {
+                vflow = s_vbuf[(s - 1) & 1][r - 1];
+            } else {
+                while (*v_filled <= u) {
+                    if (*v_abort) break;
+                }
+                __threadfence_block();
+                vflow = v_ring[u & (RING - 1)];
+                __threadfence_block();
+                if (g == 0) *v_consumed = u + 1;
+            }
+        }
+        const uint32_t hsrc = (active && u > 0) ? hflow : kFlowInvalid;
+        const bool vv = vflow != kFlowInvalid, hv = hsrc != kFlowInvalid;
+        int vx = flow_x(vflow), vy = flow_y(vflow), hx = flow_x(hsrc), hy = flow_y(hsrc);
+        clamp_flow(a.W, a.H, px, py, vx, vy);
+        clamp_flow(a.W, a.H, px, py, hx, hy);
+
+        // random search of the point finished at the previous step
+        const bool rs = row_ok && a.do_rs && pvalid && u >= 1 && u <= U;
+        int rx = 0, ry = 0;
+        const int ppx = pgx * n;
+        if (rs) {
+            const uint4 rnd = philox4x32_10(
+                make_uint4((uint32_t)(py * a.W + ppx), (uint32_t)a.t, (uint32_t)L, (uint32_t)a.dir),
+                a.seed, a.pair_id);
+            rx = flow_x(pflow) + (int)(rnd.x % span) - Rq;
+            ry = flow_y(pflow) + (int)(rnd.y % span) - Rq;
+            clamp_flow(a.W, a.H, ppx, py, rx, ry);
+        }
+
+        int ev = 0, eh = 0, er = 0;
+        if (word) {
+            const int4 na = neg64(qword);
+            if (active && vv) ev = sad_lane(a.f2L, make_tap<P>(px, py, vx, vy, L, U, V), g, na);
+            if (active && hv) eh = sad_lane(a.f2L, make_tap<P>(px, py, hx, hy, L, U, V), g, na);
+            if (rs) er = sad_lane(a.f2L, make_tap<P>(ppx, py, rx, ry, L, U, V), g, pna);
+            if (active) pna = na;
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            ev += __shfl_xor_sync(0xffffffffu, ev, o);
+            eh += __shfl_xor_sync(0xffffffffu, eh, o);
+            er += __shfl_xor_sync(0xffffffffu, er, o);
+        }
+
+        if (rs && g == 0) {
+            const size_t qidx = (size_t)gy * U + pgx;
+            if (er < pcost) {
+                a.flow[qidx] = pack_flow(rx, ry);
+                a.cost[qidx] = er;
+            } else {
+                a.flow[qidx] = pflow;
+                a.cost[qidx] = pcost;
+            }
+        }
+        if (active) {
+            uint32_t bflow = cflow;
+            int bcost = ccost;
+            if (vv && ev <= bcost) {
+                bflow = pack_flow(vx, vy);
+                bcost = ev;
+            }
+            if (hv && eh <= bcost) {
+                bflow = pack_flow(hx, hy);
+                bcost = eh;
+            }
+            if (a.do_rs) {
+                pflow = bflow;
+                pcost = bcost;
+                pgx = gx;
+                pvalid = bflow != kFlowInvalid;
+            } else if (g == 0) {
+                a.flow[pidx] = bflow;
+                a.cost[pidx] = bcost;
+            }
+            hflow = bflow;
+            if (g == 0) s_vbuf[s & 1][r] = bflow;
+            if (publish) st_relaxed_u64(edge_out + u, ((unsigned long long)a.epoch << 32) | bflow);
+        }
+        if (bar_or(*v_abort, NT)) break;
+    }
+}
+
+// level state -> caller's flow / cost arrays
+__global__ void k_export(const uint32_t *__restrict__ flow, const int *__restrict__ cost, int N,
+                         uint32_t *__restrict__ flow_out, int *__restrict__ cost_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    flow_out[i] = flow[i];
+    if (cost_out) cost_out[i] = cost[i];
+}
+
+// Sec. 3.7 forward/backward consistency: keep p iff |F(p) + F_b(q)|^2 < eps^2
+// with q the pixel nearest to p + F(p) (half up) inside the frame.
+__global__ void k_filter(const uint32_t *__restrict__ fwd, const uint32_t *__restrict__ bwd,
+                         int W, int H, int eps, uint8_t *__restrict__ mask) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H) return;
+    const int y = i / W, x = i - y * W;
+    const uint32_t f = fwd[i];
+    uint8_t m = 0;
+    if (flow_x(f) != -32768 && flow_y(f) != -32768) {
+        const int qx = x + ((flow_x(f) + 4) >> 3), qy = y + ((flow_y(f) + 4) >> 3);
+        if (qx >= 0 && qx < W && qy >= 0 && qy < H) {
+            const uint32_t b = bwd[qy * W + qx];
+            if (flow_x(b) != -32768 && flow_y(b) != -32768) {
+                const long long dx = flow_x(f) + flow_x(b), dy = flow_y(f) + flow_y(b);
+                m = (dx * dx + dy * dy < (long long)eps * eps) ? 1 : 0;
+            }
+        }
+    }
+    mask[i] = m;
+}
+
+// ============================================================================
+// host side
+// ============================================================================
+namespace {
+
+constexpr int kMaxIters = 64;
+constexpr int kMaxChunks = 64;
+constexpr int kTargetCtas = 4 * 152;
+
+struct DirState {
+    uint32_t *flow[2] = {nullptr, nullptr};   // ping-pong level state
+    int *cost[2] = {nullptr, nullptr};
+    unsigned long long *edge = nullptr;
+    unsigned int *ticket = nullptr;           // [FF_MAX_SCALES * kMaxIters]
+    int *knn_idx = nullptr;
+    int *knn_dist = nullptr;
+    int2 *part = nullptr;                     // seeding scratch
+    int *err = nullptr;
+    uint32_t epoch = 0;
+};
+
+}  // namespace
+
+struct ff_ctx {
+    ff_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    int C = 1, P = 16, S = 4, I = 4;
+    int maxW = 0, maxH = 0;
+    size_t feat_cap = 0;
+    uint8_t *feat[2] = {nullptr, nullptr};
+    int fw[2] = {0, 0}, fh[2] = {0, 0};
+    bool have[2] = {false, false};
+    DirState dir[2];
+    size_t nq_cap = 0;
+    size_t edge_cap = 0;
+    // staging for ff_pair_host
+    uint8_t *img_dev[2] = {nullptr, nullptr};
+    uint32_t *pair_flow[2] = {nullptr, nullptr};
+    uint8_t *pair_mask = nullptr;
+    unsigned long long wait_ns = 2000000000ull;
+    int force_timeout = 0;
+    long long launches = 0;
+    std::string last_error;
+    // per-launch timing (ff_profile): event pairs recorded on the launch stream
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> prof_kernel;
+    const char *pending_kernel = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+ff_status fail(ff_ctx *ctx, ff_status s, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return s;
+}
+
+ff_status check_cuda(ff_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return FF_OK;
+    return fail(ctx, FF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+const char *const kKernelNames[] = {"k_features", "k_seed_scan", "k_seed_merge",
+                                    "k_seed_rerank", "k_seed_given", "k_upsample",
+                                    "k_sweep", "k_export", "k_filter", "k_dense"};
+constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
+
+int kernel_id(const char *name) {
+    for (int i = 0; i < kNumKernels; i++)
+        if (strcmp(kKernelNames[i], name) == 0) return i;
+    return -1;
+}
+
+cudaEvent_t pool_event(ff_ctx *c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// brackets the next launch with an event pair when profiling is on
+void prof_begin(ff_ctx *c, const char *kernel) {
+    if (!c->profiling) return;
+    cudaEvent_t e = pool_event(c);
+    if (!e) return;
+    cudaEventRecord(e, c->stream);
+    c->pending_kernel = kernel;
+}
+
+ff_status check_launch(ff_ctx *ctx, const char *what) {
+    ctx->launches++;
+    const ff_status s = check_cuda(ctx, cudaGetLastError(), what);
+    if (ctx->profiling && ctx->pending_kernel) {
+        cudaEvent_t e = pool_event(ctx);
+        if (e) {
+            cudaEventRecord(e, ctx->stream);
+            ctx->prof_kernel.push_back(kernel_id(ctx->pending_kernel));
+        } else {
+            ctx->ev_used--;   // drop the unmatched start event
+        }
+        ctx->pending_kernel = nullptr;
+    }
+    return s;
+}
+
+void level_dims(int W, int H, int L, int *WL, int *HL) {
+    const int n = 1 << L;
+    *WL = (W + n - 1) / n;
+    *HL = (H + n - 1) / n;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t level_offset(int W, int H, int P, int L) {
+    size_t off = 0;
+    for (int l = 0; l < L; l++) {
+        int wl, hl;
+        level_dims(W, H, l, &wl, &hl);
+        off += align256((size_t)wl * hl * P);
+    }
+    return off;
+}
+
+int rows_per_strip(int C) { return C == 1 ? 32 : 16; }
+
+template <typename T>
+cudaError_t alloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, count * sizeof(T) + 16);
+}
+
+void free_all(ff_ctx *c) {
+    for (int s = 0; s < 2; s++) {
+        cudaFree(c->feat[s]);
+        cudaFree(c->img_dev[s]);
+        cudaFree(c->pair_flow[s]);
+        DirState &d = c->dir[s];
+        cudaFree(d.flow[0]);
+        cudaFree(d.flow[1]);
+        cudaFree(d.cost[0]);
+        cudaFree(d.cost[1]);
+        cudaFree(d.edge);
+        cudaFree(d.ticket);
+        cudaFree(d.knn_idx);
+        cudaFree(d.knn_dist);
+        cudaFree(d.part);
+        cudaFree(d.err);
+    }
+    cudaFree(c->pair_mask);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_a) cudaEventDestroy(c->ev_a);
+    if (c->ev_b) cudaEventDestroy(c->ev_b);
+}
+
+ff_status validate_config(const ff_config *c, std::string *why) {
+    if (c->patch != 8) return *why = "patch must be 8", FF_EINVAL;
+    if (c->n_coeffs != 9) return *why = "n_coeffs must be 9", FF_EINVAL;
+    if (c->channels != 1 && c->channels != 3) return *why = "channels must be 1 or 3", FF_EINVAL;
+    if (c->scales < 1 || c->scales > FF_MAX_SCALES) return *why = "scales must be 1..8", FF_EINVAL;
+    if (c->iters < 1 || c->iters > kMaxIters) return *why = "iters must be 1..64", FF_EINVAL;
+    if (c->radius_q3 < 0 || c->radius_q3 > 4096) return *why = "radius_q3 out of range", FF_EINVAL;
+    if (c->seed_leaf < 1 || c->seed_leaf > FF_MAX_LEAF) return *why = "seed_leaf must be 1..8", FF_EINVAL;
+    if (c->seed_stride < 1 || c->seed_stride > 64) return *why = "seed_stride must be 1..64", FF_EINVAL;
+    if (c->eps_q3 < 0 || c->eps_q3 > 65535) return *why = "eps_q3 out of range", FF_EINVAL;
+    if (c->max_width < 1 || c->max_width > FF_MAX_DIM || c->max_height < 1 ||
+        c->max_height > FF_MAX_DIM)
+        return *why = "max_width/max_height must be 1..4096", FF_EINVAL;
+    return FF_OK;
+}
+
+// seeding launch geometry: queries in tiles of 128, candidates split so the
+// grid holds about kTargetCtas CTAs
+void seed_geometry(int nq, int ncand, int *nchunks, int *chunk) {
+    const int qt = (nq + 127) / 128;
+    int nc = (kTargetCtas + qt - 1) / qt;
+    nc = nc < 1 ? 1 : (nc > kMaxChunks ? kMaxChunks : nc);
+    int ch = (ncand + nc - 1) / nc;
+    if (ch < 512) ch = 512;
+    *chunk = ch;
+    *nchunks = (ncand + ch - 1) / ch;
+}
+
+ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd, int W, int H) {
+    DirState &st = c->dir[d];
+    const int S = c->S, N = 1 << (S - 1);
+    int WS, HS;
+    level_dims(W, H, S - 1, &WS, &HS);
+    const int nq = WS * HS;
+    const int stride = c->cfg.seed_stride;
+    const int Wc = (W + stride - 1) / stride, Hc = (H + stride - 1) / stride;
+    const int ncand = Wc * Hc;
+    int nchunks, chunk;
+    seed_geometry(nq, ncand, &nchunks, &chunk);
+    dim3 grid((nq + 127) / 128, nchunks);
+    prof_begin(c, "k_seed_scan");
+    if (c->C == 1)
+        k_seed_scan<1><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc, ncand, chunk,
+                                                 st.part);
+    else
+        k_seed_scan<3><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc, ncand, chunk,
+                                                 st.part);
+    ff_status s = check_launch(c, "k_seed_scan");
+    if (s) return s;
+    prof_begin(c, "k_seed_merge");
+    k_seed_merge<<<(nq + 127) / 128, 128, 0, c->stream>>>(st.part, nchunks, nq, c->cfg.seed_leaf,
+                                                         st.knn_idx, st.knn_dist);
+    return check_launch(c, "k_seed_merge");
+}
+
+ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L, uint32_t *flow,
+                       int *cost, int W, int H, int L, int t, uint32_t pair_id) {
+    DirState &st = c->dir[d];
+    int WL, HL;
+    level_dims(W, H, L, &WL, &HL);
+    SweepArgs a;
+    a.f1L = f1L;
+    a.f2L = f2L;
+    a.flow = flow;
+    a.cost = cost;
+    a.edge = st.edge;
+    a.ticket = st.ticket + (size_t)L * kMaxIters + t;
+    a.err = st.err;
+    a.W = W;
+    a.H = H;
+    a.L = L;
+    a.WL = WL;
+    a.HL = HL;
+    a.d = t & 3;
+    a.t = t;
+    a.dir = d;
+    a.do_rs = t < c->I - 1;
+    a.radius_q3 = c->cfg.radius_q3;
+    a.seed = c->cfg.seed;
+    a.pair_id = pair_id;
+    a.epoch = ++st.epoch;
+    if (st.epoch == 0x7fffffffu) st.epoch = 0;   // epochs stay below bit 31
+    a.wait_ns = c->wait_ns;
+    a.force_timeout = c->force_timeout;
+    const int R = rows_per_strip(c->C);
+    const int nstrips = (HL + R - 1) / R;
+    prof_begin(c, "k_sweep");
+    if (c->C == 1)
+        k_sweep<1><<<nstrips, 160, 0, c->stream>>>(a);
+    else
+        k_sweep<3><<<nstrips, 160, 0, c->stream>>>(a);
+    return check_launch(c, "k_sweep");
+}
+
+template <int C>
+void launch_rerank(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L, int W, int H, int L,
+                   int WL, int HL, uint32_t *flow, int *cost) {
+    const int nq = WL * HL;
+    prof_begin(c, "k_seed_rerank");
+    k_seed_rerank<C><<<(nq + 127) / 128, 128, 0, c->stream>>>(
+        c->dir[d].knn_idx, c->cfg.seed_leaf, f1L, f2L, W, H, L, WL, HL, flow, cost);
+}
+
+template <int C>
+void launch_given(ff_ctx *c, const uint32_t *seeds, const uint8_t *f1L, const uint8_t *f2L, int W,
+                  int H, int L, int WL, int HL, uint32_t *flow, int *cost) {
+    const int nq = WL * HL;
+    prof_begin(c, "k_seed_given");
+    k_seed_given<C><<<(nq + 127) / 128, 128, 0, c->stream>>>(seeds, f1L, f2L, W, H, L, WL, HL, flow,
+                                                          cost);
+}
+
+template <int C>
+void launch_upsample(ff_ctx *c, const uint32_t *pflow, int WP, const uint8_t *f1L,
+                     const uint8_t *f2L, int W, int H, int L, int WL, int HL, uint32_t *flow,
+                     int *cost) {
+    const int nq = WL * HL;
+    prof_begin(c, "k_upsample");
+    k_upsample<C><<<(nq + 255) / 256, 256, 0, c->stream>>>(pflow, WP, f1L, f2L, W, H, L, WL, HL,
+                                                        flow, cost);
+}
+
+ff_status check_pair(ff_ctx *c) {
+    if (!c->have[0] || !c->have[1])
+        return fail(c, FF_ESTATE, "both frames need features (ff_features slot 0 and 1)");
+    if (c->fw[0] != c->fw[1] || c->fh[0] != c->fh[1])
+        return fail(c, FF_ESTATE, "the two frames have different sizes");
+    return FF_OK;
+}
+
+ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
+                    int until_level, int until_sweeps, int16_t *flow_out, int32_t *cost_out) {
+    ff_status s = check_pair(c);
+    if (s) return s;
+    if (dir != FF_FWD && dir != FF_BWD) return fail(c, FF_EINVAL, "dir must be FF_FWD or FF_BWD");
+    if (until_level < 0 || until_level >= c->S || until_sweeps < 0 || until_sweeps > c->I)
+        return fail(c, FF_EINVAL, "until_level/until_sweeps out of range");
+    if (!flow_out) return fail(c, FF_EINVAL, "flow_out is NULL");
+    if (((uintptr_t)flow_out & 3) || ((uintptr_t)cost_out & 3) || ((uintptr_t)seeds_in & 3))
+        return fail(c, FF_EINVAL, "flow_out, cost_out and seeds_in must be 4-byte aligned");
+    const int d = (int)dir;
+    const int W = c->fw[0], H = c->fh[0];
+    const uint8_t *fsrc = c->feat[d == 0 ? 0 : 1];
+    const uint8_t *fdst = c->feat[d == 0 ? 1 : 0];
+    DirState &st = c->dir[d];
+    s = check_cuda(c, cudaMemsetAsync(st.ticket, 0, sizeof(unsigned) * FF_MAX_SCALES * kMaxIters,
+                                      c->stream),
+                   "memset tickets");
+    if (s) return s;
+    int cur = 0, WP = 0;
+    for (int L = c->S - 1; L >= until_level; L--) {
+        int WL, HL;
+        level_dims(W, H, L, &WL, &HL);
+        const size_t off = level_offset(W, H, c->P, L);
+        const uint8_t *f1L = fsrc + off, *f2L = fdst + off;
+        uint32_t *flow = st.flow[cur];
+        int *cost = st.cost[cur];
+        if (L == c->S - 1) {
+            if (seeds_in) {
+                if (c->C == 1)
+                    launch_given<1>(c, (const uint32_t *)seeds_in, f1L, f2L, W, H, L, WL, HL, flow,
+                                    cost);
+                else
+                    launch_given<3>(c, (const uint32_t *)seeds_in, f1L, f2L, W, H, L, WL, HL, flow,
+                                    cost);
+                s = check_launch(c, "k_seed_given");
+            } else {
+                s = launch_seed_knn(c, d, fsrc, fdst, W, H);
+                if (s) return s;
+                if (c->C == 1)
+                    launch_rerank<1>(c, d, f1L, f2L, W, H, L, WL, HL, flow, cost);
+                else
+                    launch_rerank<3>(c, d, f1L, f2L, W, H, L, WL, HL, flow, cost);
+                s = check_launch(c, "k_seed_rerank");
+            }
+        } else {
+            if (c->C == 1)
+                launch_upsample<1>(c, st.flow[cur ^ 1], WP, f1L, f2L, W, H, L, WL, HL, flow, cost);
+            else
+                launch_upsample<3>(c, st.flow[cur ^ 1], WP, f1L, f2L, W, H, L, WL, HL, flow, cost);
+            s = check_launch(c, "k_upsample");
+        }
+        if (s) return s;
+        const int sweeps = (L == until_level) ? until_sweeps : c->I;
+        for (int t = 0; t < sweeps; t++) {
+            s = launch_sweep(c, d, f1L, f2L, flow, cost, W, H, L, t, pair_id);
+            if (s) return s;
+        }
+        WP = WL;
+        if (L > until_level) cur ^= 1;
+    }
+    int WL, HL;
+    level_dims(W, H, until_level, &WL, &HL);
+    const int N = WL * HL;
+    prof_begin(c, "k_export");
+    k_export<<<(N + 255) / 256, 256, 0, c->stream>>>(st.flow[cur], st.cost[cur], N,
+                                                     (uint32_t *)flow_out, (int *)cost_out);
+    return check_launch(c, "k_export");
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+ff_status ff_config_default(ff_config *cfg) {
+    if (!cfg) return FF_EINVAL;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->patch = 8;
+    cfg->n_coeffs = 9;
+    cfg->channels = 1;
+    cfg->scales = 4;
+    cfg->iters = 4;
+    cfg->radius_q3 = 8;
+    cfg->seed_leaf = 8;
+    cfg->seed_stride = 1;
+    cfg->eps_q3 = 8;
+    cfg->seed = 20261203u;
+    cfg->max_width = 1024;
+    cfg->max_height = 1024;
+    return FF_OK;
+}
+
+ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx **out) {
+    if (!cfg || !out) return FF_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (validate_config(cfg, &why) != FF_OK) return FF_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FF_ECUDA;
+    DeviceGuard guard(device);
+    ff_ctx *c = new ff_ctx();
+    c->cfg = *cfg;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->C = cfg->channels;
+    c->P = cfg->channels == 1 ? 16 : 32;
+    c->S = cfg->scales;
+    c->I = cfg->iters;
+    c->maxW = cfg->max_width;
+    c->maxH = cfg->max_height;
+    c->feat_cap = level_offset(c->maxW, c->maxH, c->P, c->S);
+    int WS, HS;
+    level_dims(c->maxW, c->maxH, c->S - 1, &WS, &HS);
+    c->nq_cap = (size_t)WS * HS;
+    const size_t npix = (size_t)c->maxW * c->maxH;
+    const int R = rows_per_strip(c->C);
+    c->edge_cap = (size_t)((c->maxH + R - 1) / R) * c->maxW;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+        e = alloc(&c->feat[s], c->feat_cap);
+        DirState &d = c->dir[s];
+        if (e == cudaSuccess) e = alloc(&d.flow[0], npix);
+        if (e == cudaSuccess) e = alloc(&d.flow[1], npix);
+        if (e == cudaSuccess) e = alloc(&d.cost[0], npix);
+        if (e == cudaSuccess) e = alloc(&d.cost[1], npix);
+        if (e == cudaSuccess) e = alloc(&d.edge, c->edge_cap);
+        if (e == cudaSuccess) e = cudaMemset(d.edge, 0, c->edge_cap * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = alloc(&d.ticket, (size_t)FF_MAX_SCALES * kMaxIters);
+        if (e == cudaSuccess) e = alloc(&d.knn_idx, c->nq_cap * FF_MAX_LEAF);
+        if (e == cudaSuccess) e = alloc(&d.knn_dist, c->nq_cap * FF_MAX_LEAF);
+        if (e == cudaSuccess) e = alloc(&d.part, c->nq_cap * kMaxChunks * 8);
+        if (e == cudaSuccess) e = alloc(&d.err, 1);
+        if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int));
+        if (e == cudaSuccess) e = alloc(&c->img_dev[s], npix * c->C);
+        if (e == cudaSuccess) e = alloc(&c->pair_flow[s], npix);
+    }
+    if (e == cudaSuccess) e = alloc(&c->pair_mask, npix);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        const ff_status s = (e == cudaErrorMemoryAllocation) ? FF_ENOMEM : FF_ECUDA;
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return s;
+    }
+    *out = c;
+    return FF_OK;
+}
+
+ff_status ff_set_stream(ff_ctx *c, void *cuda_stream) {
+    if (!c) return FF_EINVAL;
+    c->stream = (cudaStream_t)cuda_stream;
+    return FF_OK;
+}
+
+ff_status ff_features(ff_ctx *c, int slot, const uint8_t *img, int w, int h, int pitch) {
+    if (!c) return FF_EINVAL;
+    if (slot != 0 && slot != 1) return fail(c, FF_EINVAL, "slot must be 0 or 1");
+    if (!img) return fail(c, FF_EINVAL, "img is NULL");
+    if (w < 1 || h < 1 || w > c->maxW || h > c->maxH)
+        return fail(c, FF_EINVAL, "frame size exceeds the context's max_width/max_height");
+    if (pitch < w) return fail(c, FF_EINVAL, "pitch < width");
+    DeviceGuard guard(c->device);
+    c->have[slot] = false;
+    for (int L = 0; L < c->S; L++) {
+        int WL, HL;
+        level_dims(w, h, L, &WL, &HL);
+        uint8_t *out = c->feat[slot] + level_offset(w, h, c->P, L);
+        dim3 grid((WL + 15) / 16, (HL + 15) / 16), block(16, 16);
+        prof_begin(c, "k_features");
+        if (c->C == 1)
+            k_features<1><<<grid, block, 0, c->stream>>>(img, pitch, w, h, L, WL, HL, out);
+        else
+            k_features<3><<<grid, block, 0, c->stream>>>(img, pitch, w, h, L, WL, HL, out);
+        ff_status s = check_launch(c, "k_features");
+        if (s) return s;
+    }
+    c->fw[slot] = w;
+    c->fh[slot] = h;
+    c->have[slot] = true;
+    return FF_OK;
+}
+
+ff_status ff_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
+                   int16_t *flow_out, int32_t *cost_out) {
+    if (!c) return FF_EINVAL;
+    DeviceGuard guard(c->device);
+    return run_match(c, dir, pair_id, seeds_in, 0, c->I, flow_out, cost_out);
+}
+
+ff_status ff_match_until(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
+                         int until_level, int until_sweeps, int16_t *flow_out,
+                         int32_t *cost_out) {
+    if (!c) return FF_EINVAL;
+    DeviceGuard guard(c->device);
+    return run_match(c, dir, pair_id, seeds_in, until_level, until_sweeps, flow_out, cost_out);
+}
+
+ff_status ff_filter(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd,
+                    uint8_t *mask_out) {
+    if (!c) return FF_EINVAL;
+    if (!flow_fwd || !flow_bwd || !mask_out) return fail(c, FF_EINVAL, "NULL argument");
+    if (((uintptr_t)flow_fwd & 3) || ((uintptr_t)flow_bwd & 3))
+        return fail(c, FF_EINVAL, "flows must be 4-byte aligned");
+    ff_status s = check_pair(c);
+    if (s) return s;
+    DeviceGuard guard(c->device);
+    const int W = c->fw[0], H = c->fh[0], N = W * H;
+    prof_begin(c, "k_filter");
+    k_filter<<<(N + 255) / 256, 256, 0, c->stream>>>((const uint32_t *)flow_fwd,
+                                                     (const uint32_t *)flow_bwd, W, H,
+                                                     c->cfg.eps_q3, mask_out);
+    return check_launch(c, "k_filter");
+}
+
+ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_host, int w,
+                       int h, uint32_t pair_id, int16_t *flow_fwd_host, int16_t *flow_bwd_host,
+                       uint8_t *mask_host) {
+    if (!c) return FF_EINVAL;
+    if (!img1_host || !img2_host) return fail(c, FF_EINVAL, "NULL image");
+    if (w < 1 || h < 1 || w > c->maxW || h > c->maxH)
+        return fail(c, FF_EINVAL, "frame size exceeds the context's max_width/max_height");
+    DeviceGuard guard(c->device);
+    const size_t npix = (size_t)w * h, ibytes = npix * c->C;
+    cudaStream_t main = c->stream;
+    ff_status s;
+    if ((s = check_cuda(c, cudaMemcpyAsync(c->img_dev[0], img1_host, ibytes,
+                                           cudaMemcpyHostToDevice, main), "copy img1")))
+        return s;
+    if ((s = check_cuda(c, cudaMemcpyAsync(c->img_dev[1], img2_host, ibytes,
+                                           cudaMemcpyHostToDevice, main), "copy img2")))
+        return s;
+    if ((s = ff_features(c, 0, c->img_dev[0], w, h, w))) return s;
+    if ((s = ff_features(c, 1, c->img_dev[1], w, h, w))) return s;
+    // backward matching on the side stream, forward on the caller's stream
+    if ((s = check_cuda(c, cudaEventRecord(c->ev_a, main), "event"))) return s;
+    if ((s = check_cuda(c, cudaStreamWaitEvent(c->side, c->ev_a, 0), "wait"))) return s;
+    c->stream = c->side;
+    s = run_match(c, FF_BWD, pair_id, nullptr, 0, c->I, (int16_t *)c->pair_flow[1], nullptr);
+    c->stream = main;
+    if (s) return s;
+    if ((s = run_match(c, FF_FWD, pair_id, nullptr, 0, c->I, (int16_t *)c->pair_flow[0], nullptr)))
+        return s;
+    if ((s = check_cuda(c, cudaEventRecord(c->ev_b, c->side), "event"))) return s;
+    if ((s = check_cuda(c, cudaStreamWaitEvent(main, c->ev_b, 0), "wait"))) return s;
+    if ((s = ff_filter(c, (const int16_t *)c->pair_flow[0], (const int16_t *)c->pair_flow[1],
+                       c->pair_mask)))
+        return s;
+    if (flow_fwd_host &&
+        (s = check_cuda(c, cudaMemcpyAsync(flow_fwd_host, c->pair_flow[0], npix * 4,
+                                           cudaMemcpyDeviceToHost, main), "copy flow_fwd")))
+        return s;
+    if (flow_bwd_host &&
+        (s = check_cuda(c, cudaMemcpyAsync(flow_bwd_host, c->pair_flow[1], npix * 4,
+                                           cudaMemcpyDeviceToHost, main), "copy flow_bwd")))
+        return s;
+    if (mask_host &&
+        (s = check_cuda(c, cudaMemcpyAsync(mask_host, c->pair_mask, npix, cudaMemcpyDeviceToHost,
+                                           main), "copy mask")))
+        return s;
+    if ((s = check_cuda(c, cudaStreamSynchronize(main), "synchronize"))) return s;
+    int err[2] = {0, 0};
+    for (int d = 0; d < 2; d++)
+        if ((s = check_cuda(c, cudaMemcpy(&err[d], c->dir[d].err, sizeof(int),
+                                          cudaMemcpyDeviceToHost), "read error word")))
+            return s;
+    if (err[0] || err[1]) {
+        cudaMemset(c->dir[0].err, 0, sizeof(int));
+        cudaMemset(c->dir[1].err, 0, sizeof(int));
+        return fail(c, FF_ETIMEOUT, "a bounded device wait expired during matching");
+    }
+    return FF_OK;
+}
+
+ff_status ff_get_features(ff_ctx *c, int slot, int level, int8_t *dst) {
+    if (!c) return FF_EINVAL;
+    if (slot != 0 && slot != 1) return fail(c, FF_EINVAL, "slot must be 0 or 1");
+    if (level < 0 || level >= c->S) return fail(c, FF_EINVAL, "level out of range");
+    if (!c->have[slot]) return fail(c, FF_ESTATE, "slot has no features");
+    if (!dst) return fail(c, FF_EINVAL, "dst is NULL");
+    DeviceGuard guard(c->device);
+    int WL, HL;
+    level_dims(c->fw[slot], c->fh[slot], level, &WL, &HL);
+    const uint8_t *src = c->feat[slot] + level_offset(c->fw[slot], c->fh[slot], c->P, level);
+    const int N = WL * HL;
+    prof_begin(c, "k_dense");
+    if (c->C == 1)
+        k_dense<1><<<(N + 255) / 256, 256, 0, c->stream>>>(src, N, dst);
+    else
+        k_dense<3><<<(N + 255) / 256, 256, 0, c->stream>>>(src, N, dst);
+    return check_launch(c, "k_dense");
+}
+
+ff_status ff_seed_knn(ff_ctx *c, ff_dir dir, int32_t *idx_out, int32_t *dist_out) {
+    if (!c) return FF_EINVAL;
+    ff_status s = check_pair(c);
+    if (s) return s;
+    if (dir != FF_FWD && dir != FF_BWD) return fail(c, FF_EINVAL, "dir must be FF_FWD or FF_BWD");
+    if (!idx_out || !dist_out) return fail(c, FF_EINVAL, "NULL output");
+    DeviceGuard guard(c->device);
+    const int d = (int)dir, W = c->fw[0], H = c->fh[0];
+    s = launch_seed_knn(c, d, c->feat[d == 0 ? 0 : 1], c->feat[d == 0 ? 1 : 0], W, H);
+    if (s) return s;
+    int WS, HS;
+    level_dims(W, H, c->S - 1, &WS, &HS);
+    const size_t bytes = (size_t)WS * HS * c->cfg.seed_leaf * sizeof(int);
+    if ((s = check_cuda(c, cudaMemcpyAsync(idx_out, c->dir[d].knn_idx, bytes,
+                                           cudaMemcpyDeviceToDevice, c->stream), "copy knn")))
+        return s;
+    return check_cuda(c, cudaMemcpyAsync(dist_out, c->dir[d].knn_dist, bytes,
+                                         cudaMemcpyDeviceToDevice, c->stream), "copy knn");
+}
+
+ff_status ff_sync(ff_ctx *c) {
+    if (!c) return FF_EINVAL;
+    DeviceGuard guard(c->device);
+    ff_status s = check_cuda(c, cudaDeviceSynchronize(), "synchronize");
+    if (s) return s;
+    int err[2] = {0, 0};
+    for (int d = 0; d < 2; d++) {
+        s = check_cuda(c, cudaMemcpy(&err[d], c->dir[d].err, sizeof(int), cudaMemcpyDeviceToHost),
+                       "read error word");
+        if (s) return s;
+    }
+    if (err[0] || err[1]) {
+        cudaMemset(c->dir[0].err, 0, sizeof(int));
+        cudaMemset(c->dir[1].err, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        return fail(c, FF_ETIMEOUT, "a bounded device wait expired during matching");
+    }
+    return FF_OK;
+}
+
+ff_status ff_debug_set(ff_ctx *c, ff_debug_key key, long long value) {
+    if (!c) return FF_EINVAL;
+    switch (key) {
+        case FF_DEBUG_WAIT_LIMIT_NS:
+            if (value < 1000 || value > 60000000000LL)
+                return fail(c, FF_EINVAL, "wait limit must be 1 us .. 60 s");
+            c->wait_ns = (unsigned long long)value;
+            return FF_OK;
+        case FF_DEBUG_FORCE_TIMEOUT:
+            c->force_timeout = value != 0;
+            return FF_OK;
+    }
+    return fail(c, FF_EINVAL, "unknown debug key");
+}
+
+ff_status ff_profile(ff_ctx *c, int enable) {
+    if (!c) return FF_EINVAL;
+    if (enable) {
+        c->ev_used = 0;
+        c->prof_kernel.clear();
+    }
+    c->profiling = enable != 0;
+    c->pending_kernel = nullptr;
+    return FF_OK;
+}
+
+ff_status ff_kernel_stats(ff_ctx *c, const char *kernel, long long *launches, double *total_ms) {
+    if (!c || !kernel || !launches || !total_ms) return FF_EINVAL;
+    const int id = kernel_id(kernel);
+    if (id < 0) return fail(c, FF_EINVAL, std::string("unknown kernel ") + kernel);
+    DeviceGuard guard(c->device);
+    long long n = 0;
+    double ms = 0.0;
+    for (size_t k = 0; k < c->prof_kernel.size(); k++) {
+        if (c->prof_kernel[k] != id) continue;
+        float t = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&t, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]);
+        if (e != cudaSuccess) return check_cuda(c, e, "cudaEventElapsedTime");
+        n++;
+        ms += t;
+    }
+    *launches = n;
+    *total_ms = ms;
+    return FF_OK;
+}
+
+long long ff_launch_count(const ff_ctx *c) { return c ? c->launches : 0; }
+
+const char *ff_last_error(const ff_ctx *c) { return c ? c->last_error.c_str() : "NULL context"; }
+
+const char *ff_status_string(ff_status s) {
+    switch (s) {
+        case FF_OK: return "FF_OK";
+        case FF_EINVAL: return "FF_EINVAL";
+        case FF_ENOMEM: return "FF_ENOMEM";
+        case FF_ECUDA: return "FF_ECUDA";
+        case FF_ETIMEOUT: return "FF_ETIMEOUT";
+        case FF_ESTATE: return "FF_ESTATE";
+    }
+    return "unknown status";
+}
+
+void ff_destroy(ff_ctx *c) {
+    if (!c) return;
+    {
+        DeviceGuard guard(c->device);
+        cudaDeviceSynchronize();
+        free_all(c);
+    }
+    delete c;
+}
+
+}  // extern "C"

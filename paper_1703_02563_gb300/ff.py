@@ -1,0 +1,307 @@
+"""Python binding of ``libff.so`` (declared in include/ff.h).
+
+Argument marshalling only: every function here passes pointers and sizes to
+the C ABI function of the same name; all the work runs in the CUDA kernels.
+Device buffers are torch tensors (PyTorch provides device memory and
+streams); host buffers are NumPy arrays or pinned torch CPU tensors.
+
+The library is required: importing this module raises if ``libff.so`` cannot
+be built or loaded.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from dataclasses import dataclass
+
+from . import _build
+
+FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_ETIMEOUT, FF_ESTATE = range(6)
+FF_FWD, FF_BWD = 0, 1
+FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT = 1, 2
+INVALID = -32768
+
+EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
+            "ff_match_until", "ff_filter", "ff_pair_host", "ff_get_features", "ff_seed_knn",
+            "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats", "ff_launch_count",
+            "ff_last_error", "ff_status_string", "ff_destroy")
+
+
+class ff_config(ct.Structure):
+    _fields_ = [("patch", ct.c_int), ("n_coeffs", ct.c_int), ("channels", ct.c_int),
+                ("scales", ct.c_int), ("iters", ct.c_int), ("radius_q3", ct.c_int),
+                ("seed_leaf", ct.c_int), ("seed_stride", ct.c_int), ("eps_q3", ct.c_int),
+                ("seed", ct.c_uint32), ("max_width", ct.c_int), ("max_height", ct.c_int)]
+
+
+class FFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib(build: bool = True) -> ct.CDLL:
+    """Load libff.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        L = ct.CDLL(path)
+        P, i, u32 = ct.c_void_p, ct.c_int, ct.c_uint32
+        L.ff_config_default.argtypes = [ct.POINTER(ff_config)]
+        L.ff_create.argtypes = [ct.POINTER(ff_config), i, P, ct.POINTER(P)]
+        L.ff_set_stream.argtypes = [P, P]
+        L.ff_features.argtypes = [P, i, P, i, i, i]
+        L.ff_match.argtypes = [P, i, u32, P, P, P]
+        L.ff_match_until.argtypes = [P, i, u32, P, i, i, P, P]
+        L.ff_filter.argtypes = [P, P, P, P]
+        L.ff_pair_host.argtypes = [P, P, P, i, i, u32, P, P, P]
+        L.ff_get_features.argtypes = [P, i, i, P]
+        L.ff_seed_knn.argtypes = [P, i, P, P]
+        L.ff_sync.argtypes = [P]
+        L.ff_debug_set.argtypes = [P, i, ct.c_longlong]
+        L.ff_profile.argtypes = [P, i]
+        L.ff_kernel_stats.argtypes = [P, ct.c_char_p, ct.POINTER(ct.c_longlong),
+                                      ct.POINTER(ct.c_double)]
+        L.ff_launch_count.argtypes = [P]
+        L.ff_launch_count.restype = ct.c_longlong
+        L.ff_last_error.argtypes = [P]
+        L.ff_last_error.restype = ct.c_char_p
+        L.ff_status_string.argtypes = [i]
+        L.ff_status_string.restype = ct.c_char_p
+        L.ff_destroy.argtypes = [P]
+        L.ff_destroy.restype = None
+        for name in EXPORTED:
+            if name not in ("ff_last_error", "ff_status_string", "ff_destroy",
+                            "ff_launch_count"):
+                getattr(L, name).restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().ff_status_string(int(s)).decode()
+
+
+def _ptr(x) -> int | None:
+    """Address of a torch tensor, NumPy array, raw int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+@dataclass
+class Config:
+    channels: int = 1
+    scales: int = 4
+    iters: int = 4
+    radius_q3: int = 8
+    seed_leaf: int = 8
+    seed_stride: int = 1
+    eps_q3: int = 8
+    seed: int = 20261203
+    max_width: int = 1024
+    max_height: int = 1024
+    patch: int = 8
+    n_coeffs: int = 9
+
+    def c(self) -> ff_config:
+        c = ff_config()
+        lib().ff_config_default(ct.byref(c))
+        for k, v in self.__dict__.items():
+            setattr(c, k, int(v))
+        return c
+
+
+def ff_config_default() -> Config:
+    c = ff_config()
+    _check(None, lib().ff_config_default(ct.byref(c)))
+    return Config(**{k: getattr(c, k) for k, _ in ff_config._fields_})
+
+
+def _check(ctx, status: int):
+    if status != FF_OK:
+        msg = lib().ff_last_error(ctx).decode() if ctx else ""
+        raise FFError(status, msg)
+
+
+def ff_create(cfg: Config, device: int = 0, stream=None) -> int:
+    out = ct.c_void_p()
+    c = cfg.c()
+    _check(None, lib().ff_create(ct.byref(c), device, _stream_handle(stream), ct.byref(out)))
+    return out.value
+
+
+def ff_set_stream(ctx: int, stream) -> None:
+    _check(ctx, lib().ff_set_stream(ctx, _stream_handle(stream)))
+
+
+def ff_features(ctx: int, slot: int, img, w: int, h: int, pitch: int) -> None:
+    _check(ctx, lib().ff_features(ctx, slot, _ptr(img), w, h, pitch))
+
+
+def ff_match(ctx: int, direction: int, pair_id: int, seeds_in, flow_out, cost_out=None) -> None:
+    _check(ctx, lib().ff_match(ctx, direction, pair_id, _ptr(seeds_in), _ptr(flow_out),
+                               _ptr(cost_out)))
+
+
+def ff_match_until(ctx: int, direction: int, pair_id: int, seeds_in, until_level: int,
+                   until_sweeps: int, flow_out, cost_out=None) -> None:
+    _check(ctx, lib().ff_match_until(ctx, direction, pair_id, _ptr(seeds_in), until_level,
+                                     until_sweeps, _ptr(flow_out), _ptr(cost_out)))
+
+
+def ff_filter(ctx: int, flow_fwd, flow_bwd, mask_out) -> None:
+    _check(ctx, lib().ff_filter(ctx, _ptr(flow_fwd), _ptr(flow_bwd), _ptr(mask_out)))
+
+
+def ff_pair_host(ctx: int, img1_host, img2_host, w: int, h: int, pair_id: int,
+                 flow_fwd_host=None, flow_bwd_host=None, mask_host=None) -> None:
+    _check(ctx, lib().ff_pair_host(ctx, _ptr(img1_host), _ptr(img2_host), w, h, pair_id,
+                                   _ptr(flow_fwd_host), _ptr(flow_bwd_host), _ptr(mask_host)))
+
+
+def ff_get_features(ctx: int, slot: int, level: int, dst) -> None:
+    _check(ctx, lib().ff_get_features(ctx, slot, level, _ptr(dst)))
+
+
+def ff_seed_knn(ctx: int, direction: int, idx_out, dist_out) -> None:
+    _check(ctx, lib().ff_seed_knn(ctx, direction, _ptr(idx_out), _ptr(dist_out)))
+
+
+def ff_sync(ctx: int) -> None:
+    _check(ctx, lib().ff_sync(ctx))
+
+
+def ff_debug_set(ctx: int, key: int, value: int) -> None:
+    _check(ctx, lib().ff_debug_set(ctx, key, value))
+
+
+def ff_profile(ctx: int, enable: bool) -> None:
+    _check(ctx, lib().ff_profile(ctx, 1 if enable else 0))
+
+
+def ff_kernel_stats(ctx: int, kernel: str) -> tuple[int, float]:
+    """(launches, summed device ms) of `kernel` recorded since ff_profile(ctx, 1)."""
+    n = ct.c_longlong(0)
+    ms = ct.c_double(0.0)
+    _check(ctx, lib().ff_kernel_stats(ctx, kernel.encode(), ct.byref(n), ct.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+KERNELS = ("k_features", "k_seed_scan", "k_seed_merge", "k_seed_rerank", "k_seed_given",
+           "k_upsample", "k_sweep", "k_export", "k_filter", "k_dense")
+
+
+def ff_launch_count(ctx: int) -> int:
+    return int(lib().ff_launch_count(ctx))
+
+
+def ff_last_error(ctx: int) -> str:
+    return lib().ff_last_error(ctx).decode()
+
+
+def ff_destroy(ctx: int) -> None:
+    lib().ff_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
+# a small convenience layer over the same calls (torch device tensors)
+# ----------------------------------------------------------------------------
+def level_dims(w: int, h: int, level: int) -> tuple[int, int]:
+    n = 1 << level
+    return (w + n - 1) // n, (h + n - 1) // n
+
+
+class Context:
+    """Owns one ff_ctx; frames and outputs are torch CUDA tensors."""
+
+    def __init__(self, cfg: Config, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.ctx = ff_create(cfg, device, stream)
+        self.size = None
+
+    def close(self):
+        if self.ctx:
+            ff_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def features(self, slot: int, img) -> None:
+        """img: uint8 CUDA tensor [C][H][W] (contiguous)."""
+        assert img.is_cuda and img.dtype == self.torch.uint8 and img.is_contiguous()
+        C, H, W = img.shape
+        assert C == self.cfg.channels
+        ff_features(self.ctx, slot, img, W, H, W)
+        self.size = (W, H)
+
+    def match(self, direction: int, pair_id: int = 0, seeds_in=None, until_level: int = 0,
+              until_sweeps: int | None = None, with_cost: bool = True):
+        torch = self.torch
+        W, H = self.size
+        if until_sweeps is None:
+            until_sweeps = self.cfg.iters
+        WL, HL = level_dims(W, H, until_level)
+        dev = torch.device("cuda", self.device)
+        flow = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
+        cost = torch.empty((HL, WL), dtype=torch.int32, device=dev) if with_cost else None
+        if until_level == 0 and until_sweeps == self.cfg.iters:
+            ff_match(self.ctx, direction, pair_id, seeds_in, flow, cost)
+        else:
+            ff_match_until(self.ctx, direction, pair_id, seeds_in, until_level, until_sweeps,
+                           flow, cost)
+        return flow, cost
+
+    def filter(self, flow_fwd, flow_bwd):
+        torch = self.torch
+        W, H = self.size
+        mask = torch.empty((H, W), dtype=torch.uint8, device=flow_fwd.device)
+        ff_filter(self.ctx, flow_fwd, flow_bwd, mask)
+        return mask
+
+    def features_of(self, slot: int, level: int):
+        torch = self.torch
+        W, H = self.size
+        WL, HL = level_dims(W, H, level)
+        out = torch.empty((HL, WL, 9 * self.cfg.channels), dtype=torch.int8,
+                          device=torch.device("cuda", self.device))
+        ff_get_features(self.ctx, slot, level, out)
+        return out
+
+    def seed_knn(self, direction: int):
+        torch = self.torch
+        W, H = self.size
+        WS, HS = level_dims(W, H, self.cfg.scales - 1)
+        dev = torch.device("cuda", self.device)
+        idx = torch.empty((HS, WS, self.cfg.seed_leaf), dtype=torch.int32, device=dev)
+        dist = torch.empty_like(idx)
+        ff_seed_knn(self.ctx, direction, idx, dist)
+        return idx, dist
+
+    def sync(self):
+        ff_sync(self.ctx)
