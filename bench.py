@@ -185,6 +185,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     main = torch.cuda.Stream(dev)
     side = torch.cuda.Stream(dev)
     ctx = ff.ff_create(cfg, local_rank, main)
+    if args.sweep_warps:
+        ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WARPS, args.sweep_warps)
     img1 = torch.from_numpy(pair.img1).to(dev)
     img2 = torch.from_numpy(pair.img2).to(dev)
     flow_f = torch.empty((H, W, 2), dtype=torch.int16, device=dev)
@@ -313,6 +315,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-warps", type=int, default=0,
+                    help="propagation warps per sweep CTA (1, 2, 4; 0 = library default)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -141,11 +141,17 @@ ff_status ff_seed_knn(ff_ctx *ctx, ff_dir dir, int32_t *idx_out, int32_t *dist_o
  * device wait expired since the last ff_sync (and clears the record). */
 ff_status ff_sync(ff_ctx *ctx);
 
-/* Test hooks.  FF_DEBUG_WAIT_LIMIT_NS: upper bound of every device-side
- * wait (default 2 s).  FF_DEBUG_FORCE_TIMEOUT: when nonzero, the next
- * propagation sweeps wait for a boundary row that is never written, so the
- * bounded wait runs out and ff_sync reports FF_ETIMEOUT. */
-typedef enum { FF_DEBUG_WAIT_LIMIT_NS = 1, FF_DEBUG_FORCE_TIMEOUT = 2 } ff_debug_key;
+/* Test and tuning hooks.  FF_DEBUG_WAIT_LIMIT_NS: upper bound of every
+ * device-side wait (default 2 s).  FF_DEBUG_FORCE_TIMEOUT: when nonzero, the
+ * next propagation sweeps wait for a boundary row that is never written, so
+ * the bounded wait runs out and ff_sync reports FF_ETIMEOUT.
+ * FF_DEBUG_SWEEP_WARPS: propagation warps per sweep CTA (1, 2 or 4; default
+ * 1); every value gives the same results. */
+typedef enum {
+    FF_DEBUG_WAIT_LIMIT_NS = 1,
+    FF_DEBUG_FORCE_TIMEOUT = 2,
+    FF_DEBUG_SWEEP_WARPS = 3
+} ff_debug_key;
 ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
 
 /* Per-launch timing for measurement.  While enabled, every kernel launch

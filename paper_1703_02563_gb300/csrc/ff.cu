@@ -119,38 +119,41 @@ __device__ __forceinline__ void list_insert(int (&D)[8], int (&I)[8], int d, int
     }
 }
 
-// Phase 1: one query per thread, one candidate chunk per blockIdx.y.
-// Candidates of the chunk are staged 256 at a time in shared memory with
-// their squared norms; |q - c|^2 = |q|^2 + |c|^2 - 2 q.c with q.c by dp4a.
-template <int C>
+// Phase 1: QPT queries per thread (a tile of 128*QPT queries per CTA), one
+// candidate chunk per blockIdx.y.  Candidates of the chunk are staged 256 at
+// a time in shared memory with their squared norms.  Since
+// |q - c|^2 = |q|^2 + |c|^2 - 2 q.c and |q|^2 is fixed per query, the lists
+// are kept on the key |c|^2 - 2 q.c (one dp4a per 4 dimensions for q.c) and
+// |q|^2 is added on output.  Within a chunk candidates arrive in increasing
+// linear index, so a strict compare against the list's worst key keeps the
+// (distance, index) order.
+template <int C, int QPT>
 __global__ void __launch_bounds__(128)
     k_seed_scan(const uint8_t *__restrict__ f1, const uint8_t *__restrict__ f2, int W, int N,
                 int WS, int NQ, int stride, int Wc, int ncand, int chunk, int2 *__restrict__ part) {
     constexpr int P = Geo<C>::P, NV = P / 16, NW = Geo<C>::NW, TILE = 256;
     __shared__ uint4 s_w[TILE][NV];
-    __shared__ int s_n[TILE];
-    __shared__ int s_i[TILE];
-    const int q = blockIdx.x * 128 + threadIdx.x;
-    uint32_t qw[P / 4];
-    int qn = 0;
-    {
-        const int qq = min(q, NQ - 1);
-        const int gy = qq / WS, gx = qq - gy * WS;
-        const uint4 *src = reinterpret_cast<const uint4 *>(f1 + ((size_t)gy * N * W + gx * N) * P);
+    __shared__ int2 s_ni[TILE];   // (norm, linear index)
+    uint32_t qw[QPT][NW];
+    int thr[QPT];
+    int D[QPT][8], I[QPT][8];
 #pragma unroll
-        for (int k = 0; k < NV; k++) {
-            const uint4 v = __ldg(src + k);
-            qw[4 * k] = v.x;
-            qw[4 * k + 1] = v.y;
-            qw[4 * k + 2] = v.z;
-            qw[4 * k + 3] = v.w;
+    for (int j = 0; j < QPT; j++) {
+        const int q = min((blockIdx.x * QPT + j) * 128 + threadIdx.x, NQ - 1);
+        const int gy = q / WS, gx = q - gy * WS;
+        const uint32_t *src =
+            reinterpret_cast<const uint32_t *>(f1 + ((size_t)gy * N * W + gx * N) * P);
+        int qn = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            qw[j][w] = __ldg(src + w);
+            qn = __dp4a((int)qw[j][w], (int)qw[j][w], qn);
         }
+        (void)qn;
+        thr[j] = 0x7fffffff;   // the list's worst key; INT32_MAX while not full
 #pragma unroll
-        for (int w = 0; w < NW; w++) qn = __dp4a((int)qw[w], (int)qw[w], qn);
+        for (int k = 0; k < 8; k++) D[j][k] = I[j][k] = 0x7fffffff;
     }
-    int D[8], I[8];
-#pragma unroll
-    for (int k = 0; k < 8; k++) D[k] = I[k] = 0x7fffffff;
     const int c0 = blockIdx.y * chunk, c1 = min(c0 + chunk, ncand);
     for (int base = c0; base < c1; base += TILE) {
         __syncthreads();
@@ -169,31 +172,47 @@ __global__ void __launch_bounds__(128)
                     nn = __dp4a((int)x.z, (int)x.z, nn);
                     nn = __dp4a((int)x.w, (int)x.w, nn);
                 }
-                s_n[k] = nn;
-                s_i[k] = cy * W + cx;
+                s_ni[k] = make_int2(nn, cy * W + cx);
             }
         }
         __syncthreads();
         const int cnt = min(TILE, c1 - base);
         for (int k = 0; k < cnt; k++) {
-            int dot = 0;
+            uint32_t cw[NV * 4];
 #pragma unroll
             for (int v = 0; v < NV; v++) {
                 const uint4 x = s_w[k][v];
-                dot = __dp4a((int)qw[4 * v], (int)x.x, dot);
-                dot = __dp4a((int)qw[4 * v + 1], (int)x.y, dot);
-                dot = __dp4a((int)qw[4 * v + 2], (int)x.z, dot);
-                dot = __dp4a((int)qw[4 * v + 3], (int)x.w, dot);
+                cw[4 * v] = x.x;
+                cw[4 * v + 1] = x.y;
+                cw[4 * v + 2] = x.z;
+                cw[4 * v + 3] = x.w;
             }
-            const int dist = qn + s_n[k] - 2 * dot;
-            const int idx = s_i[k];
-            if (lex_less(dist, idx, D[7], I[7])) list_insert(D, I, dist, idx);
+            const int2 ni = s_ni[k];
+#pragma unroll
+            for (int j = 0; j < QPT; j++) {
+                int dot = 0;
+#pragma unroll
+                for (int w = 0; w < NW; w++) dot = __dp4a((int)qw[j][w], (int)cw[w], dot);
+                const int key = ni.x - 2 * dot;
+                if (key < thr[j]) {
+                    // the list stores |c|^2 - 2 q.c; |q|^2 is added on output
+                    list_insert(D[j], I[j], key, ni.y);
+                    thr[j] = D[j][7];
+                }
+            }
         }
     }
-    if (q < NQ) {
+#pragma unroll
+    for (int j = 0; j < QPT; j++) {
+        const int q = (blockIdx.x * QPT + j) * 128 + threadIdx.x;
+        if (q >= NQ) continue;
+        int qn = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) qn = __dp4a((int)qw[j][w], (int)qw[j][w], qn);
         int2 *dst = part + ((size_t)blockIdx.y * NQ + q) * 8;
 #pragma unroll
-        for (int k = 0; k < 8; k++) dst[k] = make_int2(D[k], I[k]);
+        for (int k = 0; k < 8; k++)
+            dst[k] = make_int2(I[j][k] == 0x7fffffff ? 0x7fffffff : D[j][k] + qn, I[j][k]);
     }
 }
 
@@ -303,237 +322,7 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
     cost[q] = sad_full<C>(f2L, make_tap<P>(px, py, flow_x(f), flow_y(f), L, WL, HL), qw);
 }
 
-// ---------------------------------------------------------------------------
-// propagation sweep + random search (Sec. 3.1 Eq. 2, Sec. 3.2)
-// ---------------------------------------------------------------------------
-struct SweepArgs {
-    const uint8_t *f1L;
-    const uint8_t *f2L;
-    uint32_t *flow;                // level state, updated in place
-    int *cost;
-    unsigned long long *edge;      // [nstrips][WL] boundary rows: (epoch << 32) | flow
-    unsigned int *ticket;          // strip counter of this launch (zeroed before)
-    int *err;                      // error word of this direction
-    int W, H, L, WL, HL;
-    int d, t, dir, do_rs, radius_q3;
-    uint32_t seed, pair_id, epoch;
-    unsigned long long wait_ns;
-    int force_timeout;
-};
-
-// One sweep in direction d, followed (when do_rs) by the random search.
-//
-// The sweep runs in its own frame (u, v): u along the sweep's x order, v
-// along its y order, so every direction has sources (u-1, v) and (u, v-1)
-// and the raster order v-major.  Point (u, v) depends only on those two, so
-// all points of one anti-diagonal are independent; the kernel reproduces the
-// raster order exactly as a skewed wavefront:
-//   * a CTA owns a strip of R consecutive rows; row r handles column
-//     u = s - r at step s, so (u, v-1) was finished by row r-1 one step
-//     earlier and (u-1, v) by row r itself;
-//   * each point is evaluated by G lanes, one 4-dimension word each, reduced
-//     with xor shuffles; rows hand their result down through shared memory
-//     with one named barrier per step;
-//   * the strip's last row publishes its sweep results as 64-bit words
-//     tagged with this launch's epoch; a loader warp of the next strip polls
-//     them into a shared ring ahead of use, so no global wait or fence sits
-//     on the per-step critical path.  Strips are handed out by a ticket
-//     counter, so a strip only ever waits on a strip that is already running.
-//   * the random search of point (u-1, v) is evaluated one step later,
-//     alongside the sweep of (u, v); it uses the sweep value, and only its
-//     result (never seen by neighbours in this sweep) goes to memory.
-// Every wait is bounded (wait_ns without progress); on expiry the error word
-// gets FF_ETIMEOUT and every strip of the launch returns early.
-template <int C>
-__global__ void __launch_bounds__(160) k_sweep(const SweepArgs a) {
-    constexpr int P = Geo<C>::P, NW = Geo<C>::NW, G = Geo<C>::G;
-    constexpr int NT = 128, R = NT / G, RING = 128;
-    __shared__ uint32_t s_vbuf[2][R];
-    __shared__ uint32_t s_ring[RING];
-    __shared__ int s_filled, s_consumed, s_abort, s_strip;
-    volatile int *v_filled = &s_filled;
-    volatile int *v_consumed = &s_consumed;
-    volatile int *v_abort = &s_abort;
-    volatile uint32_t *v_ring = s_ring;
-
-    const int tid = threadIdx.x;
-    const int U = a.WL, V = a.HL;
-    const int nstrips = (V + R - 1) / R;
-    if (tid == 0) {
-        s_strip = (int)atomicAdd(a.ticket, 1u);
-        s_filled = 0;
-        s_consumed = 0;
-        s_abort = 0;
-    }
-    __syncthreads();
-    const int strip = s_strip;
-    if (strip >= nstrips) return;
-    const int v0 = strip * R;
-
-    if (tid >= NT) {
-        // ---------------- loader warp: previous strip's last row -> ring
-        if (strip == 0) return;
-        const int lane = tid - NT;
-        const unsigned long long *src = a.edge + (size_t)(strip - 1) * U;
-        const uint32_t want = (a.force_timeout && strip == 1) ? (a.epoch ^ 0x80000000u) : a.epoch;
-        int base = 0;
-        unsigned long long t0 = globaltimer_ns();
-        while (base < U) {
-            const int col = base + lane;
-            const int limit = *v_consumed + RING;
-            bool ready = col >= U;
-            uint32_t val = 0;
-            if (col < U && col < limit) {
-                const unsigned long long e = ld_relaxed_u64(src + col);
-                ready = (uint32_t)(e >> 32) == want;
-                val = (uint32_t)e;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, ready);
-            int nready = (m == 0xffffffffu) ? 32 : (__ffs(~m) - 1);
-            nready = min(nready, U - base);
-            if (lane < nready) v_ring[col & (RING - 1)] = val;
-            __syncwarp();
-            if (nready > 0) {
-                __threadfence_block();
-                base += nready;
-                if (lane == 0) *v_filled = base;
-                t0 = globaltimer_ns();
-            } else {
-                int stop = 0;
-                if (lane == 0) {
-                    const bool late = globaltimer_ns() - t0 > a.wait_ns;
-                    if (late) atomicCAS(a.err, 0, kErrTimeout);
-                    stop = late || ld_relaxed_i32(a.err) != 0;
-                    if (stop) *v_abort = 1;
-                }
-                if (__shfl_sync(0xffffffffu, stop, 0)) return;
-                __nanosleep(64);
-            }
-        }
-        return;
-    }
-
-    // ---------------- compute warps
-    const int r = tid / G, g = tid - (tid / G) * G;
-    const int v = v0 + r;
-    const bool row_ok = v < V;
-    const int L = a.L, n = 1 << L;
-    const bool word = g < NW;
-    const bool flipx = (a.d == 1 || a.d == 2), flipy = (a.d == 1 || a.d == 3);
-    const int gy = row_ok ? (flipy ? V - 1 - v : v) : 0;
-    const int py = gy * n;
-    const int Rq = a.radius_q3 * n;
-    const uint32_t span = 2u * (uint32_t)Rq + 1u;
-    const bool publish = (r == R - 1) && (strip + 1 < nstrips) && (g == 0);
-    unsigned long long *edge_out = a.edge + (size_t)strip * U;
-
-    uint32_t hflow = kFlowInvalid;      // sweep value of (u-1, v)
-    uint32_t pflow = kFlowInvalid;      // pending random search: sweep value ...
-    int pcost = kCostInvalid;           // ... its cost
-    int pgx = 0;                        // ... its grid x
-    int4 pna = make_int4(0, 0, 0, 0);   // ... its query word (x -64)
-    bool pvalid = false;
-
-    const int nsteps = U + R;
-    for (int s = 0; s < nsteps; s++) {
-        const int u = s - r;
-        const bool active = row_ok && u >= 0 && u < U;
-        const int gx = flipx ? U - 1 - u : u;
-        const int px = gx * n;
-        const size_t pidx = (size_t)gy * U + gx;
-
-        uint32_t cflow = kFlowInvalid, qword = 0;
-        int ccost = kCostInvalid;
-        if (active) {
-            cflow = a.flow[pidx];
-            ccost = a.cost[pidx];
-            if (word) qword = ldg32(a.f1L + pidx * P + 4 * g);
-        }
-        uint32_t vflow = kFlowInvalid;
-        if (active && v > 0) {
-            if (r > 0) {
-                vflow = s_vbuf[(s - 1) & 1][r - 1];
-            } else {
-                while (*v_filled <= u) {
-                    if (*v_abort) break;
-                }
-                __threadfence_block();
-                vflow = v_ring[u & (RING - 1)];
-                __threadfence_block();
-                if (g == 0) *v_consumed = u + 1;
-            }
-        }
-        const uint32_t hsrc = (active && u > 0) ? hflow : kFlowInvalid;
-        const bool vv = vflow != kFlowInvalid, hv = hsrc != kFlowInvalid;
-        int vx = flow_x(vflow), vy = flow_y(vflow), hx = flow_x(hsrc), hy = flow_y(hsrc);
-        clamp_flow(a.W, a.H, px, py, vx, vy);
-        clamp_flow(a.W, a.H, px, py, hx, hy);
-
-        // random search of the point finished at the previous step
-        const bool rs = row_ok && a.do_rs && pvalid && u >= 1 && u <= U;
-        int rx = 0, ry = 0;
-        const int ppx = pgx * n;
-        if (rs) {
-            const uint4 rnd = philox4x32_10(
-                make_uint4((uint32_t)(py * a.W + ppx), (uint32_t)a.t, (uint32_t)L, (uint32_t)a.dir),
-                a.seed, a.pair_id);
-            rx = flow_x(pflow) + (int)(rnd.x % span) - Rq;
-            ry = flow_y(pflow) + (int)(rnd.y % span) - Rq;
-            clamp_flow(a.W, a.H, ppx, py, rx, ry);
-        }
-
-        int ev = 0, eh = 0, er = 0;
-        if (word) {
-            const int4 na = neg64(qword);
-            if (active && vv) ev = sad_lane(a.f2L, make_tap<P>(px, py, vx, vy, L, U, V), g, na);
-            if (active && hv) eh = sad_lane(a.f2L, make_tap<P>(px, py, hx, hy, L, U, V), g, na);
-            if (rs) er = sad_lane(a.f2L, make_tap<P>(ppx, py, rx, ry, L, U, V), g, pna);
-            if (active) pna = na;
-        }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            ev += __shfl_xor_sync(0xffffffffu, ev, o);
-            eh += __shfl_xor_sync(0xffffffffu, eh, o);
-            er += __shfl_xor_sync(0xffffffffu, er, o);
-        }
-
-        if (rs && g == 0) {
-            const size_t qidx = (size_t)gy * U + pgx;
-            if (er < pcost) {
-                a.flow[qidx] = pack_flow(rx, ry);
-                a.cost[qidx] = er;
-            } else {
-                a.flow[qidx] = pflow;
-                a.cost[qidx] = pcost;
-            }
-        }
-        if (active) {
-            uint32_t bflow = cflow;
-            int bcost = ccost;
-            if (vv && ev <= bcost) {
-                bflow = pack_flow(vx, vy);
-                bcost = ev;
-            }
-            if (hv && eh <= bcost) {
-                bflow = pack_flow(hx, hy);
-                bcost = eh;
-            }
-            if (a.do_rs) {
-                pflow = bflow;
-                pcost = bcost;
-                pgx = gx;
-                pvalid = bflow != kFlowInvalid;
-            } else if (g == 0) {
-                a.flow[pidx] = bflow;
-                a.cost[pidx] = bcost;
-            }
-            hflow = bflow;
-            if (g == 0) s_vbuf[s & 1][r] = bflow;
-            if (publish) st_relaxed_u64(edge_out + u, ((unsigned long long)a.epoch << 32) | bflow);
-        }
-        if (bar_or(*v_abort, NT)) break;
-    }
-}
+#include "ff_sweep.cuh"
 
 // level state -> caller's flow / cost arrays
 __global__ void k_export(const uint32_t *__restrict__ flow, const int *__restrict__ cost, int N,
@@ -573,7 +362,9 @@ namespace {
 
 constexpr int kMaxIters = 64;
 constexpr int kMaxChunks = 64;
-constexpr int kTargetCtas = 4 * 152;
+constexpr int kTargetCtas = 8 * 152;
+constexpr int kSeedQpt = 2;
+constexpr int kSeedQueriesPerCta = 128 * kSeedQpt;
 
 struct DirState {
     uint32_t *flow[2] = {nullptr, nullptr};   // ping-pong level state
@@ -609,6 +400,7 @@ struct ff_ctx {
     uint32_t *pair_flow[2] = {nullptr, nullptr};
     uint8_t *pair_mask = nullptr;
     unsigned long long wait_ns = 2000000000ull;
+    int sweep_warps = 1;   // propagation warps per sweep CTA: 1, 2 or 4
     int force_timeout = 0;
     long long launches = 0;
     std::string last_error;
@@ -706,7 +498,11 @@ size_t level_offset(int W, int H, int P, int L) {
     return off;
 }
 
-int rows_per_strip(int C) { return C == 1 ? 32 : 16; }
+// rows per strip of the sweep kernel for `np` propagation warps per CTA
+int rows_per_strip(int C, int np) {
+    const int rw = C == 1 ? SweepGeo<1, 1>::RW : SweepGeo<3, 1>::RW;
+    return rw * np;
+}
 
 template <typename T>
 cudaError_t alloc(T **p, size_t count) {
@@ -744,7 +540,7 @@ ff_status validate_config(const ff_config *c, std::string *why) {
     if (c->channels != 1 && c->channels != 3) return *why = "channels must be 1 or 3", FF_EINVAL;
     if (c->scales < 1 || c->scales > FF_MAX_SCALES) return *why = "scales must be 1..8", FF_EINVAL;
     if (c->iters < 1 || c->iters > kMaxIters) return *why = "iters must be 1..64", FF_EINVAL;
-    if (c->radius_q3 < 0 || c->radius_q3 > 4096) return *why = "radius_q3 out of range", FF_EINVAL;
+    if (c->radius_q3 < 0 || c->radius_q3 > 255) return *why = "radius_q3 must be 0..255", FF_EINVAL;
     if (c->seed_leaf < 1 || c->seed_leaf > FF_MAX_LEAF) return *why = "seed_leaf must be 1..8", FF_EINVAL;
     if (c->seed_stride < 1 || c->seed_stride > 64) return *why = "seed_stride must be 1..64", FF_EINVAL;
     if (c->eps_q3 < 0 || c->eps_q3 > 65535) return *why = "eps_q3 out of range", FF_EINVAL;
@@ -757,7 +553,7 @@ ff_status validate_config(const ff_config *c, std::string *why) {
 // seeding launch geometry: queries in tiles of 128, candidates split so the
 // grid holds about kTargetCtas CTAs
 void seed_geometry(int nq, int ncand, int *nchunks, int *chunk) {
-    const int qt = (nq + 127) / 128;
+    const int qt = (nq + kSeedQueriesPerCta - 1) / kSeedQueriesPerCta;
     int nc = (kTargetCtas + qt - 1) / qt;
     nc = nc < 1 ? 1 : (nc > kMaxChunks ? kMaxChunks : nc);
     int ch = (ncand + nc - 1) / nc;
@@ -777,14 +573,14 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
     const int ncand = Wc * Hc;
     int nchunks, chunk;
     seed_geometry(nq, ncand, &nchunks, &chunk);
-    dim3 grid((nq + 127) / 128, nchunks);
+    dim3 grid((nq + kSeedQueriesPerCta - 1) / kSeedQueriesPerCta, nchunks);
     prof_begin(c, "k_seed_scan");
     if (c->C == 1)
-        k_seed_scan<1><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc, ncand, chunk,
-                                                 st.part);
+        k_seed_scan<1, kSeedQpt><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc,
+                                                             ncand, chunk, st.part);
     else
-        k_seed_scan<3><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc, ncand, chunk,
-                                                 st.part);
+        k_seed_scan<3, kSeedQpt><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc,
+                                                             ncand, chunk, st.part);
     ff_status s = check_launch(c, "k_seed_scan");
     if (s) return s;
     prof_begin(c, "k_seed_merge");
@@ -822,13 +618,21 @@ ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L,
     if (st.epoch == 0x7fffffffu) st.epoch = 0;   // epochs stay below bit 31
     a.wait_ns = c->wait_ns;
     a.force_timeout = c->force_timeout;
-    const int R = rows_per_strip(c->C);
+    const int R = rows_per_strip(c->C, c->sweep_warps);
     const int nstrips = (HL + R - 1) / R;
     prof_begin(c, "k_sweep");
-    if (c->C == 1)
-        k_sweep<1><<<nstrips, 160, 0, c->stream>>>(a);
-    else
-        k_sweep<3><<<nstrips, 160, 0, c->stream>>>(a);
+#define FF_LAUNCH_SWEEP(CC, NPW) \
+    k_sweep<CC, NPW><<<nstrips, SweepGeo<CC, NPW>::THREADS, 0, c->stream>>>(a)
+    if (c->C == 1) {
+        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(1, 1);
+        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(1, 2);
+        else FF_LAUNCH_SWEEP(1, 4);
+    } else {
+        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(3, 1);
+        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(3, 2);
+        else FF_LAUNCH_SWEEP(3, 4);
+    }
+#undef FF_LAUNCH_SWEEP
     return check_launch(c, "k_sweep");
 }
 
@@ -986,7 +790,7 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     level_dims(c->maxW, c->maxH, c->S - 1, &WS, &HS);
     c->nq_cap = (size_t)WS * HS;
     const size_t npix = (size_t)c->maxW * c->maxH;
-    const int R = rows_per_strip(c->C);
+    const int R = rows_per_strip(c->C, 1);   // the smallest strip
     c->edge_cap = (size_t)((c->maxH + R - 1) / R) * c->maxW;
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < 2 && e == cudaSuccess; s++) {
@@ -1217,6 +1021,11 @@ ff_status ff_debug_set(ff_ctx *c, ff_debug_key key, long long value) {
             return FF_OK;
         case FF_DEBUG_FORCE_TIMEOUT:
             c->force_timeout = value != 0;
+            return FF_OK;
+        case FF_DEBUG_SWEEP_WARPS:
+            if (value != 1 && value != 2 && value != 4)
+                return fail(c, FF_EINVAL, "sweep warps must be 1, 2 or 4");
+            c->sweep_warps = (int)value;
             return FF_OK;
     }
     return fail(c, FF_EINVAL, "unknown debug key");

@@ -17,7 +17,7 @@ from . import _build
 
 FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_ETIMEOUT, FF_ESTATE = range(6)
 FF_FWD, FF_BWD = 0, 1
-FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT = 1, 2
+FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS = 1, 2, 3
 INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",

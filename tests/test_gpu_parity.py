@@ -123,6 +123,27 @@ def test_every_stage_bit_exact_lab_multistrip():
     ctx.close()
 
 
+@pytest.mark.parametrize("warps", [1, 2, 4])
+@pytest.mark.parametrize("C", [1, 3])
+def test_sweep_warp_variants_bit_exact(C, warps):
+    # every CTA shape of the sweep kernel gives the oracle's result
+    if C == 1:
+        pair = workloads.translation_pair(seed=31, width=150, height=77)
+    else:
+        pair = workloads.layered_pair(seed=31, width=101, height=67, channels=3, max_disp=18)
+    S, I = 3, 5
+    ctx = _ctx(C, S, I, pair.width, pair.height)
+    ff.ff_debug_set(ctx.ctx, ff.FF_DEBUG_SWEEP_WARPS, warps)
+    _load(ctx, pair)
+    P = _params(C, S, I)
+    for d, (a, b) in enumerate(((pair.img1, pair.img2), (pair.img2, pair.img1))):
+        flow, cost = ctx.match(d, 4)
+        rf, rc, _ = O.match(P, a, b, d, 4)
+        np.testing.assert_array_equal(_host(flow), rf)
+        np.testing.assert_array_equal(_host(cost), rc)
+    ctx.close()
+
+
 FULL_CASES = [
     ("tiny", lambda: workloads.make_workload("tiny128x96")[0], 1, 3, 4, 8),
     ("lab97x71", lambda: workloads.layered_pair(seed=4, width=97, height=71, channels=3,
