@@ -137,6 +137,33 @@ ff_status ff_get_features(ff_ctx *ctx, int slot, int level, int8_t *dst);
  * [H_c][W_c][l] (squared feature distance), ascending by (dist, idx). */
 ff_status ff_seed_knn(ff_ctx *ctx, ff_dir dir, int32_t *idx_out, int32_t *dist_out);
 
+/* Allocation-free seeding search.  The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory, for example code
+ * that runs while a stream is being captured, a real-time loop that must not
+ * wait on the allocator, or a host program that hands the library a fixed
+ * memory budget and owns every allocation itself.  It computes what
+ * ff_seed_knn computes, without a context, and allocates nothing: its
+ * scratch (the per-chunk partial lists) is an 8 MiB array in the library's
+ * static device memory, which every GPU that loads the library holds until
+ * the process exits.
+ *  feat_src0 / feat_dst0: level-0 features of the query and the candidate
+ *    frame, int8 [h][w][P] (P = 16 for 1 channel, 32 for 3: the 9*channels
+ *    codes of ff_get_features, then zero bytes), 16-byte aligned.
+ *  idx_out / dist_out: int32 [H_c][W_c][leaf], as ff_seed_knn.
+ *  cuda_stream: the stream to enqueue on (NULL = legacy default stream).
+ *  why: NULL, or receives a static message when the call is rejected.
+ * The first call on a device looks up the scratch's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the scratch, which keeps the last call's contents, so
+ * calls that overlap on a GPU race: order them on one stream.  Nothing in the
+ * scratch needs clearing: each call writes every list it reads.  Returns
+ * FF_EINVAL (nothing launched) for bad arguments, including more than 131072
+ * coarsest-grid points, which is the scratch limit, and FF_ECUDA if the
+ * set-up or a launch fails. */
+ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, int w, int h,
+                             int channels, int scales, int leaf, int stride, int32_t *idx_out,
+                             int32_t *dist_out, void *cuda_stream, const char **why);
+
 /* Blocks until the context's work is done; returns FF_ETIMEOUT if a bounded
  * device wait expired since the last ff_sync (and clears the record). */
 ff_status ff_sync(ff_ctx *ctx);

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -745,6 +746,39 @@ ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seed
 }  // namespace
 
 // ============================================================================
+// allocation-free seeding search (ff_seed_knn_static)
+// ============================================================================
+namespace {
+
+// Scratch of the allocation-free seeding search: the per-chunk partial top-8
+// lists, 8 MiB.  It lives in this file's static device memory, so every GPU
+// that loads the library holds it until the process exits.  Every call
+// shares it; calls that overlap on a GPU race on it.
+constexpr size_t kStaticScratchInt2 = (size_t)1 << 20;   // 8 MiB of int2
+static __device__ __align__(256) int2 g_seed_scratch[kStaticScratchInt2];
+
+// In host code g_seed_scratch names a host-side stand-in, not device memory:
+// the kernels get the device address, looked up once per device (with that
+// device current) and cached here.
+std::mutex g_scratch_mutex;
+int2 *g_scratch_ptr[64] = {nullptr};
+
+cudaError_t static_scratch(int device, int2 **out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_seed_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[device] = (int2 *)ptr;
+    }
+    *out = g_scratch_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// ============================================================================
 // C ABI
 // ============================================================================
 extern "C" {
@@ -989,6 +1023,62 @@ ff_status ff_seed_knn(ff_ctx *c, ff_dir dir, int32_t *idx_out, int32_t *dist_out
         return s;
     return check_cuda(c, cudaMemcpyAsync(dist_out, c->dir[d].knn_dist, bytes,
                                          cudaMemcpyDeviceToDevice, c->stream), "copy knn");
+}
+
+ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, int w, int h,
+                             int channels, int scales, int leaf, int stride, int32_t *idx_out,
+                             int32_t *dist_out, void *cuda_stream, const char **why) {
+    const char *dummy = nullptr;
+    const char **msg = why ? why : &dummy;
+    *msg = "";
+    if (!feat_src0 || !feat_dst0 || !idx_out || !dist_out)
+        return *msg = "a pointer argument is NULL", FF_EINVAL;
+    if (channels != 1 && channels != 3) return *msg = "channels must be 1 or 3", FF_EINVAL;
+    if (w < 1 || h < 1 || w > FF_MAX_DIM || h > FF_MAX_DIM)
+        return *msg = "frame size must be 1..4096 in each direction", FF_EINVAL;
+    if (scales < 1 || scales > FF_MAX_SCALES) return *msg = "scales must be 1..8", FF_EINVAL;
+    if (leaf < 1 || leaf > FF_MAX_LEAF) return *msg = "leaf must be 1..8", FF_EINVAL;
+    if (stride < 1 || stride > 64) return *msg = "stride must be 1..64", FF_EINVAL;
+    if (((uintptr_t)feat_src0 & 15) || ((uintptr_t)feat_dst0 & 15))
+        return *msg = "feature arrays must be 16-byte aligned", FF_EINVAL;
+    if (((uintptr_t)idx_out & 3) || ((uintptr_t)dist_out & 3))
+        return *msg = "outputs must be 4-byte aligned", FF_EINVAL;
+    int WS, HS;
+    level_dims(w, h, scales - 1, &WS, &HS);
+    const size_t nq = (size_t)WS * HS;
+    const size_t max_slots = kStaticScratchInt2 / 8;   // (chunk, query) lists that fit
+    if (nq > max_slots)
+        return *msg = "too many coarsest-grid points for the static scratch (limit 131072)",
+               FF_EINVAL;
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    int2 *scratch = nullptr;
+    if (e == cudaSuccess) e = static_scratch(device, &scratch);
+    if (e != cudaSuccess) return *msg = "device set-up failed", FF_ECUDA;
+    const int N = 1 << (scales - 1);
+    const int Wc = (w + stride - 1) / stride, Hc = (h + stride - 1) / stride;
+    const int ncand = Wc * Hc;
+    int nchunks, chunk;
+    seed_geometry((int)nq, ncand, &nchunks, &chunk);
+    const int cap = (int)(max_slots / nq);
+    if (nchunks > cap) {
+        chunk = (ncand + cap - 1) / cap;
+        nchunks = (ncand + chunk - 1) / chunk;
+    }
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const uint8_t *fs = (const uint8_t *)feat_src0, *fd = (const uint8_t *)feat_dst0;
+    dim3 grid((unsigned)((nq + kSeedQueriesPerCta - 1) / kSeedQueriesPerCta), nchunks);
+    if (channels == 1)
+        k_seed_scan<1, kSeedQpt><<<grid, 128, 0, stream>>>(fs, fd, w, N, WS, (int)nq, stride, Wc,
+                                                          ncand, chunk, scratch);
+    else
+        k_seed_scan<3, kSeedQpt><<<grid, 128, 0, stream>>>(fs, fd, w, N, WS, (int)nq, stride, Wc,
+                                                          ncand, chunk, scratch);
+    k_seed_merge<<<(unsigned)((nq + 127) / 128), 128, 0, stream>>>(scratch, nchunks, (int)nq, leaf,
+                                                                  idx_out, dist_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return *msg = "kernel launch failed", FF_ECUDA;
+    return FF_OK;
 }
 
 ff_status ff_sync(ff_ctx *c) {

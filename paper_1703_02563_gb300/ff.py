@@ -22,8 +22,8 @@ INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
             "ff_match_until", "ff_filter", "ff_pair_host", "ff_get_features", "ff_seed_knn",
-            "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats", "ff_launch_count",
-            "ff_last_error", "ff_status_string", "ff_destroy")
+            "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
+            "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy")
 
 
 class ff_config(ct.Structure):
@@ -59,6 +59,8 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_pair_host.argtypes = [P, P, P, i, i, u32, P, P, P]
         L.ff_get_features.argtypes = [P, i, i, P]
         L.ff_seed_knn.argtypes = [P, i, P, P]
+        L.ff_seed_knn_static.argtypes = [P, P, i, i, i, i, i, i, P, P, P,
+                                         ct.POINTER(ct.c_char_p)]
         L.ff_sync.argtypes = [P]
         L.ff_debug_set.argtypes = [P, i, ct.c_longlong]
         L.ff_profile.argtypes = [P, i]
@@ -182,6 +184,17 @@ def ff_get_features(ctx: int, slot: int, level: int, dst) -> None:
 
 def ff_seed_knn(ctx: int, direction: int, idx_out, dist_out) -> None:
     _check(ctx, lib().ff_seed_knn(ctx, direction, _ptr(idx_out), _ptr(dist_out)))
+
+
+def ff_seed_knn_static(feat_src0, feat_dst0, w: int, h: int, channels: int, scales: int,
+                       leaf: int, stride: int, idx_out, dist_out, stream=None) -> None:
+    """Allocation-free seeding search (no context; see include/ff.h)."""
+    why = ct.c_char_p()
+    st = lib().ff_seed_knn_static(_ptr(feat_src0), _ptr(feat_dst0), w, h, channels, scales, leaf,
+                                  stride, _ptr(idx_out), _ptr(dist_out), _stream_handle(stream),
+                                  ct.byref(why))
+    if st != FF_OK:
+        raise FFError(st, (why.value or b"").decode())
 
 
 def ff_sync(ctx: int) -> None:
