@@ -185,7 +185,7 @@ ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
  * is bracketed by a pair of CUDA events on the stream it is launched on.
  * ff_profile(ctx, 1) clears the record and starts recording; ff_profile(ctx,
  * 0) stops.  ff_kernel_stats (call after ff_sync) returns, for the kernel
- * named `kernel` ("k_features", "k_seed_scan", "k_seed_merge",
+ * named `kernel` ("k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge",
  * "k_seed_rerank", "k_seed_given", "k_upsample", "k_sweep", "k_export",
  * "k_filter", "k_dense"), the number of recorded launches and their summed
  * device time in milliseconds. */

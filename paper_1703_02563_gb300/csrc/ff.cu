@@ -324,6 +324,7 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
 }
 
 #include "ff_sweep.cuh"
+#include "ff_seed.cuh"
 
 // level state -> caller's flow / cost arrays
 __global__ void k_export(const uint32_t *__restrict__ flow, const int *__restrict__ cost, int N,
@@ -365,6 +366,7 @@ constexpr int kMaxIters = 64;
 constexpr int kMaxChunks = 64;
 constexpr int kTargetCtas = 8 * 152;
 constexpr int kSeedQpt = 2;
+constexpr int kSeedSample = 16;   // candidate subsampling of the bound pass
 constexpr int kSeedQueriesPerCta = 128 * kSeedQpt;
 
 struct DirState {
@@ -374,7 +376,11 @@ struct DirState {
     unsigned int *ticket = nullptr;           // [FF_MAX_SCALES * kMaxIters]
     int *knn_idx = nullptr;
     int *knn_dist = nullptr;
-    int2 *part = nullptr;                     // seeding scratch
+    int2 *part = nullptr;                     // seeding scratch: per-chunk lists
+    __nv_bfloat16 *qbf = nullptr;             // seeding queries, bf16 rows of K
+    int *qnorm = nullptr;                     //   their squared norms
+    float *t0 = nullptr;                      //   upper bounds of their 8th key
+    __nv_bfloat16 *cbf = nullptr;             // seeding candidates, bf16 rows of K
     int *err = nullptr;
     uint32_t epoch = 0;
 };
@@ -436,7 +442,7 @@ ff_status check_cuda(ff_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, FF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-const char *const kKernelNames[] = {"k_features", "k_seed_scan", "k_seed_merge",
+const char *const kKernelNames[] = {"k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge",
                                     "k_seed_rerank", "k_seed_given", "k_upsample",
                                     "k_sweep", "k_export", "k_filter", "k_dense"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
@@ -525,6 +531,10 @@ void free_all(ff_ctx *c) {
         cudaFree(d.knn_idx);
         cudaFree(d.knn_dist);
         cudaFree(d.part);
+        cudaFree(d.qbf);
+        cudaFree(d.qnorm);
+        cudaFree(d.t0);
+        cudaFree(d.cbf);
         cudaFree(d.err);
     }
     cudaFree(c->pair_mask);
@@ -563,6 +573,20 @@ void seed_geometry(int nq, int ncand, int *nchunks, int *chunk) {
     *nchunks = (ncand + ch - 1) / ch;
 }
 
+// seeding geometry of the tensor-core scan: 128 queries per CTA, candidates
+// split into chunks (whole 64-candidate tiles) so the grid holds about
+// kTargetCtas CTAs
+void seed_geometry_mma(int nq, int ncand, int *nchunks, int *chunk) {
+    const int qt = (nq + 63) / 64;
+    int nc = (4 * 152 + qt - 1) / qt;   // about four CTAs per SM: long chunks, few restarts
+    nc = nc < 1 ? 1 : (nc > kMaxChunks ? kMaxChunks : nc);
+    int ch = (ncand + nc - 1) / nc;
+    ch = ((ch + 63) / 64) * 64;
+    if (ch < 512) ch = 512;
+    *chunk = ch;
+    *nchunks = (ncand + ch - 1) / ch;
+}
+
 ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd, int W, int H) {
     DirState &st = c->dir[d];
     const int S = c->S, N = 1 << (S - 1);
@@ -572,17 +596,57 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
     const int stride = c->cfg.seed_stride;
     const int Wc = (W + stride - 1) / stride, Hc = (H + stride - 1) / stride;
     const int ncand = Wc * Hc;
+    // bf16 rows of the queries (coarsest grid) and candidates (stride grid)
+    prof_begin(c, "k_seed_prep");
+    if (c->C == 1)
+        k_seed_prep<1, 16, true><<<(nq + 127) / 128, 128, 0, c->stream>>>(fs, W, N, WS, HS, st.qbf,
+                                                                         st.qnorm);
+    else
+        k_seed_prep<3, 32, true><<<(nq + 127) / 128, 128, 0, c->stream>>>(fs, W, N, WS, HS, st.qbf,
+                                                                         st.qnorm);
+    ff_status s = check_launch(c, "k_seed_prep");
+    if (s) return s;
+    prof_begin(c, "k_seed_prep");
+    if (c->C == 1)
+        k_seed_prep<1, 16, false><<<(ncand + 127) / 128, 128, 0, c->stream>>>(
+            fd, W, stride, Wc, Hc, st.cbf, nullptr);
+    else
+        k_seed_prep<3, 32, false><<<(ncand + 127) / 128, 128, 0, c->stream>>>(
+            fd, W, stride, Wc, Hc, st.cbf, nullptr);
+    s = check_launch(c, "k_seed_prep");
+    if (s) return s;
+    // bound pass over every kSeedSample-th candidate: the 8th key of each
+    // chunk of the sample bounds the query's final 8th key from above
+    const int ns = (ncand + kSeedSample - 1) / kSeedSample;
+    int nchunks1, chunk1;
+    seed_geometry_mma(nq, ns, &nchunks1, &chunk1);
+    {
+        dim3 grid1((nq + 63) / 64, nchunks1);
+        prof_begin(c, "k_seed_scan");
+        if (c->C == 1)
+            k_seed_mma<1><<<grid1, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ns, chunk1,
+                                                        kSeedSample, W, stride, Wc, nullptr, 0,
+                                                        st.t0, st.part);
+        else
+            k_seed_mma<2><<<grid1, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ns, chunk1,
+                                                        kSeedSample, W, stride, Wc, nullptr, 0,
+                                                        st.t0, st.part);
+        s = check_launch(c, "k_seed_scan");
+        if (s) return s;
+    }
     int nchunks, chunk;
-    seed_geometry(nq, ncand, &nchunks, &chunk);
-    dim3 grid((nq + kSeedQueriesPerCta - 1) / kSeedQueriesPerCta, nchunks);
+    seed_geometry_mma(nq, ncand, &nchunks, &chunk);
+    dim3 grid((nq + 63) / 64, nchunks);
     prof_begin(c, "k_seed_scan");
     if (c->C == 1)
-        k_seed_scan<1, kSeedQpt><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc,
-                                                             ncand, chunk, st.part);
+        k_seed_mma<1><<<grid, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ncand, chunk, 1,
+                                                   W, stride, Wc, st.t0, nchunks1, nullptr,
+                                                   st.part);
     else
-        k_seed_scan<3, kSeedQpt><<<grid, 128, 0, c->stream>>>(fs, fd, W, N, WS, nq, stride, Wc,
-                                                             ncand, chunk, st.part);
-    ff_status s = check_launch(c, "k_seed_scan");
+        k_seed_mma<2><<<grid, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ncand, chunk, 1,
+                                                   W, stride, Wc, st.t0, nchunks1, nullptr,
+                                                   st.part);
+    s = check_launch(c, "k_seed_scan");
     if (s) return s;
     prof_begin(c, "k_seed_merge");
     k_seed_merge<<<(nq + 127) / 128, 128, 0, c->stream>>>(st.part, nchunks, nq, c->cfg.seed_leaf,
@@ -840,6 +904,11 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
         if (e == cudaSuccess) e = alloc(&d.knn_idx, c->nq_cap * FF_MAX_LEAF);
         if (e == cudaSuccess) e = alloc(&d.knn_dist, c->nq_cap * FF_MAX_LEAF);
         if (e == cudaSuccess) e = alloc(&d.part, c->nq_cap * kMaxChunks * 8);
+        const size_t K = c->C == 1 ? 16 : 32;
+        if (e == cudaSuccess) e = alloc(&d.qbf, c->nq_cap * K);
+        if (e == cudaSuccess) e = alloc(&d.qnorm, c->nq_cap);
+        if (e == cudaSuccess) e = alloc(&d.t0, c->nq_cap * kMaxChunks);
+        if (e == cudaSuccess) e = alloc(&d.cbf, npix * K);
         if (e == cudaSuccess) e = alloc(&d.err, 1);
         if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int));
         if (e == cudaSuccess) e = alloc(&c->img_dev[s], npix * c->C);

@@ -217,7 +217,7 @@ def ff_kernel_stats(ctx: int, kernel: str) -> tuple[int, float]:
     return int(n.value), float(ms.value)
 
 
-KERNELS = ("k_features", "k_seed_scan", "k_seed_merge", "k_seed_rerank", "k_seed_given",
+KERNELS = ("k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge", "k_seed_rerank", "k_seed_given",
            "k_upsample", "k_sweep", "k_export", "k_filter", "k_dense")
 
 

@@ -71,7 +71,8 @@ def test_features_bit_exact(C, W, H, S):
 
 
 @pytest.mark.parametrize("C,W,H,S,stride", [(1, 128, 96, 3, 1), (3, 97, 71, 3, 2),
-                                            (1, 45, 33, 2, 1), (3, 20, 12, 1, 3)])
+                                            (1, 45, 33, 2, 1), (3, 20, 12, 1, 3),
+                                            (3, 200, 120, 3, 1), (1, 301, 77, 2, 1)])
 def test_seed_knn_bit_exact(C, W, H, S, stride):
     if C == 1:
         pair = workloads.translation_pair(seed=W, width=W, height=H) if W >= 64 else \
