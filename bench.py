@@ -264,47 +264,77 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
             "prm": prm, "pair": pair}
 
 
+ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock (Tops/s)
+
+
+def sweep_evals(W: int, H: int, S: int, I: int) -> int:
+    """Cost evaluations of all propagation sweeps + random searches of one
+    direction: per level, I sweeps of 2 candidates per point (one fewer on
+    the two incoming borders) and I-1 random searches of 1 candidate."""
+    n = 0
+    for L in range(S):
+        s = 1 << L
+        wl, hl = (W + s - 1) // s, (H + s - 1) // s
+        n += I * (2 * wl * hl - wl - hl) + (I - 1) * wl * hl
+    return n
+
+
+def recorded_traffic(kernel: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    sources are unchanged since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")) as f:
+            rec = json.load(f)
+        src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["sources"])
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def roofline(res: dict, steps: int) -> dict:
     """Roofline of the kernel with the largest share of device time.
 
     k_sweep (propagation + random search) is integer-ALU work on a serial
-    wavefront: algorithmic work = cost evaluations x 10 integer ops per
-    feature dimension (4 multiply-adds of the bilinear taps, subtract,
-    absolute value, accumulate = 7 ops; counted as 10 with the tap and
-    weight arithmetic amortised per dimension), peak = 152 SMs x 64 INT32
-    lanes x 2.07 GHz.  k_seed_scan is a dense int8 contraction: 2 ops per
-    multiply-add of (query dims) x (candidates) x (queries), same peak x 4
-    (one dp4a = 4 multiply-adds).
+    wavefront.  Algorithmic work per evaluation: per feature dimension 4
+    multiply-adds of the bilinear taps, a subtraction, an absolute value and
+    an accumulation (7 int ops), plus 3 ops of tap/weight arithmetic
+    amortised per dimension = 10 int ops; evaluations per launch from
+    sweep_evals.  Peak: 152 SMs x 64 INT32 lanes x 2.07 GHz.
+    k_seed_scan (the tensor-core seeding) is a dense contraction: 2 flops per
+    multiply-add of (queries x candidates x K), against the measured bf16
+    tensor peak.
     """
     ks = res["kstats"]
     tot = {k: v[1] for k, v in ks.items()}
     dom = max(tot, key=lambda k: tot[k])
     n_launch, ms = ks[dom]
     W, H, C, S, I = res["W"], res["H"], res["C"], res["S"], res["I"]
-    dims = 9 * C
-    alu_peak_tops = 152 * 64 * 2.07e9 / 1e12
+    share = ms / sum(tot.values())
+    avg_ms = ms / max(n_launch, 1)
     if dom == "k_sweep":
-        evals = 2 * eval_count(W, H, S, I, 8) - 2 * 8 * ((W + (1 << (S - 1)) - 1) >> (S - 1)) * \
-            ((H + (1 << (S - 1)) - 1) >> (S - 1))
-        ops = evals * dims * 10 * steps
-        achieved = ops / (ms / 1e3) / 1e12
-        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak_tops,
-                "unit": "Tops/s", "frac": achieved / alu_peak_tops, "traffic": None,
-                "launches": n_launch, "avg_launch_ms": ms / max(n_launch, 1),
-                "share": ms / sum(tot.values())}
+        ops_per_launch = 2 * steps * sweep_evals(W, H, S, I) * 9 * C * 10 / max(n_launch, 1)
+        achieved = ops_per_launch / (avg_ms / 1e3) / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
+                "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
+                "traffic": recorded_traffic(dom), "launches": n_launch, "avg_launch_ms": avg_ms,
+                "share": share, "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2.07 GHz"}
     if dom == "k_seed_scan":
         N = 1 << (S - 1)
         nq = ((W + N - 1) // N) * ((H + N - 1) // N)
-        macs = 2 * nq * W * H * dims * steps
-        achieved = 2 * macs / (ms / 1e3) / 1e12
-        peak = alu_peak_tops * 4 * 2
-        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
-                "launches": n_launch, "avg_launch_ms": ms / max(n_launch, 1),
-                "share": ms / sum(tot.values())}
-    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak_tops,
+        K = 16 if C == 1 else 32
+        flops = 2 * steps * 2 * nq * W * H * K * 2 * (1 + 1 / 16) / max(n_launch, 1)
+        peak = measured_peaks().get("bf16_tflops", 1900.0)
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        return {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "launches": n_launch, "avg_launch_ms": avg_ms, "share": share,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": ALU_PEAK_TOPS,
             "unit": "Tops/s", "frac": None, "traffic": None, "launches": n_launch,
-            "avg_launch_ms": ms / max(n_launch, 1), "share": ms / sum(tot.values())}
+            "avg_launch_ms": avg_ms, "share": share}
 
 
 def main():
