@@ -275,6 +275,30 @@ int ffo_seed_knn_rows(const int8_t *f1_0, const int8_t *f2_0, int C, int W, int 
     return filled_max;
 }
 
+/* Sweep schedules.
+ * basic (Sec. 3.1-3.2): `iters` sweeps with radius R, a random search after
+ *   each but the last.
+ * Flow Fields+ (Sec. 3.3): 4 sweeps with R+ = 2R (3 random searches), then 8
+ *   sweeps with R (7 random searches); the four directions repeat every 4.
+ * Flow Fields+ Fast (Sec. 3.4): as Flow Fields+, but the finest scale runs
+ *   only 4 sweeps with R (3 random searches). */
+int ffo_schedule_sweeps(int schedule, int iters, int L) {
+    if (schedule == 1) return 12;
+    if (schedule == 2) return L == 0 ? 4 : 12;
+    return iters;
+}
+
+int ffo_schedule_radius_mult(int schedule, int L, int t) {
+    if (schedule == 1 || (schedule == 2 && L > 0)) return t < 4 ? 2 : 1;
+    return 1;
+}
+
+int ffo_schedule_rs_after(int schedule, int iters, int L, int t) {
+    const int n = ffo_schedule_sweeps(schedule, iters, L);
+    if (schedule == 1 || (schedule == 2 && L > 0)) return t != 3 && t != n - 1;
+    return t < n - 1;
+}
+
 typedef struct {
     int16_t *fx, *fy;
     int32_t *cost;
@@ -433,10 +457,11 @@ int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *
                        int W, int H, int dir, uint32_t pair_id, const int16_t *seeds_in,
                        int until_level, int until_sweeps,
                        int16_t *flow_out, int32_t *cost_out, int64_t *evals_out) {
-    int C = prm->channels, S = prm->scales, I = prm->iters;
+    int C = prm->channels, S = prm->scales, I = prm->iters, sch = prm->schedule;
     if (W < 1 || H < 1 || W > 4096 || H > 4096 || (C != 1 && C != 3) || S < 1 || S > 8 ||
         I < 1 || prm->seed_leaf < 1 || prm->seed_stride < 1 || prm->radius_q3 < 0 ||
-        until_level < 0 || until_level >= S || until_sweeps < 0 || until_sweeps > I)
+        sch < 0 || sch > 2 || until_level < 0 || until_level >= S || until_sweeps < 0 ||
+        until_sweeps > ffo_schedule_sweeps(sch, I, until_level))
         return 1;
     int64_t evals = 0;
     int WL, HL, WP = 0, HP = 0;
@@ -514,12 +539,13 @@ int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *
             free(prev.fy);
             free(prev.cost);
         }
-        int sweeps = (L == until_level) ? until_sweeps : I;
+        int sweeps = (L == until_level) ? until_sweeps : ffo_schedule_sweeps(sch, I, L);
         for (int t = 0; t < sweeps; t++) {
             sweep(f1L, f2L, C, W, H, L, t % 4, &cur, &evals);
-            if (t < I - 1)
-                random_search(f1L, f2L, C, W, H, L, t, dir, prm->radius_q3, prm->seed, pair_id,
-                              &cur, &evals);
+            if (ffo_schedule_rs_after(sch, I, L, t))
+                random_search(f1L, f2L, C, W, H, L, t, dir,
+                              prm->radius_q3 * ffo_schedule_radius_mult(sch, L, t), prm->seed,
+                              pair_id, &cur, &evals);
         }
         prev = cur;
         WP = WL;
@@ -576,4 +602,16 @@ void ffo_filter(const int16_t *fwd, const int16_t *bwd, int W, int H, int eps_q3
             long ddx = Fx + Bx, ddy = Fy + By;
             mask[i] = (ddx * ddx + ddy * ddy < (long)eps_q3 * eps_q3) ? 1 : 0;
         }
+}
+
+/* Sec. 3.7: with two backward flows (different random streams), a pixel is
+ * deleted if it is not consistent with either of them. */
+void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, int W, int H,
+                 int eps_q3, uint8_t *mask) {
+    long n = (long)W * H;
+    uint8_t *m2 = (uint8_t *)malloc((size_t)n);
+    ffo_filter(fwd, bwd1, W, H, eps_q3, mask);
+    ffo_filter(fwd, bwd2, W, H, eps_q3, m2);
+    for (long i = 0; i < n; i++) mask[i] = (uint8_t)(mask[i] & m2[i]);
+    free(m2);
 }

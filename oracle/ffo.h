@@ -35,7 +35,15 @@ typedef struct {
     int seed_leaf;    /* l: candidates kept by the seeding search  */
     int seed_stride;  /* sigma: candidate grid stride in image 2   */
     uint32_t seed;    /* Philox key word 0                         */
+    int schedule;     /* 0 basic, 1 Flow Fields+, 2 Flow Fields+ Fast */
 } ffo_params;
+
+/* The sweep schedule of one level: number of sweeps, and for sweep t the
+ * random-search radius multiplier (1 or 2) and whether a random search
+ * follows it. */
+int ffo_schedule_sweeps(int schedule, int iters, int L);
+int ffo_schedule_radius_mult(int schedule, int L, int t);
+int ffo_schedule_rs_after(int schedule, int iters, int L, int t);
 
 /* level grid size for scale n = 2^L: ceil(W/n) x ceil(H/n) */
 void ffo_level_dims(int W, int H, int L, int *WL, int *HL);
@@ -84,10 +92,12 @@ void ffo_random_search_level(const int8_t *f1L, const int8_t *f2L, int C, int W,
                              int16_t *flow, int32_t *cost, int64_t *evals);
 
 /* Full matching of src -> dst features (all levels, concatenated).
- * dir: 0 forward, 1 backward (Philox counter word 3).  seeds_in: NULL or
- * int16 [H_{S-1}][W_{S-1}][2] flows replacing the seeding search.
- * Stops at level until_level after until_sweeps sweeps (each followed by its
- * random search when one follows it); the defaults are 0 and iters.  Writes
+ * dir: 0 forward, 1 backward, 2 second backward (Philox counter word 3;
+ * Sec. 3.7's second backward flow differs from the first only in its random
+ * stream).  seeds_in: NULL or int16 [H_{S-1}][W_{S-1}][2] flows replacing the
+ * seeding search.  Stops at level until_level after until_sweeps sweeps (each
+ * followed by its random search when one follows it); the defaults are 0 and
+ * the schedule's sweep count of level 0.  Writes
  * that level's grid: flow_out int16 [HL][WL][2], cost_out int32 [HL][WL].
  * evals (may be NULL) receives the number of cost evaluations performed.
  * Returns 0 on success, nonzero on bad arguments. */
@@ -105,6 +115,9 @@ int ffo_match(const ffo_params *prm, const uint8_t *src, const uint8_t *dst, int
 /* forward/backward consistency check: mask 1 keeps a pixel */
 void ffo_filter(const int16_t *fwd, const int16_t *bwd, int W, int H, int eps_q3,
                 uint8_t *mask);
+/* two backward flows: a pixel is kept only if consistent with both */
+void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, int W, int H,
+                 int eps_q3, uint8_t *mask);
 
 #ifdef __cplusplus
 }

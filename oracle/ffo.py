@@ -49,6 +49,13 @@ def lib():
         L.ffo_match.argtypes = [P, P, P, i, i, i, ct.c_uint32, P, i, i, P, P, P]
         L.ffo_match.restype = i
         L.ffo_filter.argtypes = [P, P, i, i, i, P]
+        L.ffo_filter2.argtypes = [P, P, P, i, i, i, P]
+        L.ffo_schedule_sweeps.argtypes = [i, i, i]
+        L.ffo_schedule_sweeps.restype = i
+        L.ffo_schedule_radius_mult.argtypes = [i, i, i]
+        L.ffo_schedule_radius_mult.restype = i
+        L.ffo_schedule_rs_after.argtypes = [i, i, i, i]
+        L.ffo_schedule_rs_after.restype = i
         L.ffo_sweep_level.argtypes = [P, P, i, i, i, i, i, P, P, P]
         L.ffo_random_search_level.argtypes = [P, P, i, i, i, i, i, i, i, ct.c_uint32,
                                               ct.c_uint32, P, P, P]
@@ -59,7 +66,7 @@ def lib():
 class _Params(ct.Structure):
     _fields_ = [("channels", ct.c_int), ("scales", ct.c_int), ("iters", ct.c_int),
                 ("radius_q3", ct.c_int), ("seed_leaf", ct.c_int), ("seed_stride", ct.c_int),
-                ("seed", ct.c_uint32)]
+                ("seed", ct.c_uint32), ("schedule", ct.c_int)]
 
 
 @dataclass
@@ -71,10 +78,14 @@ class Params:
     seed_leaf: int = 8
     seed_stride: int = 1
     seed: int = 20261203
+    schedule: int = 0   # 0 basic, 1 Flow Fields+, 2 Flow Fields+ Fast
 
     def c(self) -> _Params:
         return _Params(self.channels, self.scales, self.iters, self.radius_q3,
-                       self.seed_leaf, self.seed_stride, self.seed)
+                       self.seed_leaf, self.seed_stride, self.seed, self.schedule)
+
+    def sweeps(self, level: int) -> int:
+        return int(lib().ffo_schedule_sweeps(self.schedule, self.iters, level))
 
 
 def _p(a: np.ndarray):
@@ -189,7 +200,7 @@ def match_features(prm: Params, fsrc: list[np.ndarray], fdst: list[np.ndarray], 
                    until_level: int = 0, until_sweeps: int | None = None):
     """Returns (flow int16 [HL][WL][2], cost int32 [HL][WL], evals)."""
     if until_sweeps is None:
-        until_sweeps = prm.iters
+        until_sweeps = prm.sweeps(until_level)
     WL, HL = level_dims(W, H, until_level)
     flow = np.zeros((HL, WL, 2), np.int16)
     cst = np.zeros((HL, WL), np.int32)
@@ -216,7 +227,7 @@ def match(prm: Params, src: np.ndarray, dst: np.ndarray, direction: int = 0, pai
     C, H, W = src.shape
     assert C == prm.channels and dst.shape == src.shape
     if until_sweeps is None:
-        until_sweeps = prm.iters
+        until_sweeps = prm.sweeps(until_level)
     WL, HL = level_dims(W, H, until_level)
     flow = np.zeros((HL, WL, 2), np.int16)
     cst = np.zeros((HL, WL), np.int32)
@@ -265,3 +276,14 @@ def random_search_level(f1L, f2L, W: int, H: int, L: int, t: int, direction: int
     lib().ffo_random_search_level(_p(f1L), _p(f2L), f1L.shape[-1] // 9, W, H, L, t, direction,
                                   radius_q3, seed, pair_id, _p(flow), _p(cost), ct.byref(ev))
     return flow, cost, ev.value
+
+
+def filter_mask2(fwd: np.ndarray, bwd1: np.ndarray, bwd2: np.ndarray, eps_q3: int) -> np.ndarray:
+    """Two-way check: consistent with both backward flows."""
+    fwd = np.ascontiguousarray(fwd, np.int16)
+    bwd1 = np.ascontiguousarray(bwd1, np.int16)
+    bwd2 = np.ascontiguousarray(bwd2, np.int16)
+    H, W, _ = fwd.shape
+    mask = np.zeros((H, W), np.uint8)
+    lib().ffo_filter2(_p(fwd), _p(bwd1), _p(bwd2), W, H, eps_q3, _p(mask))
+    return mask

@@ -515,3 +515,77 @@ def test_seeds_in_replace_search():
     fwd, _, _ = O.match(P, pair.img1, pair.img2, 0, 0, seeds_in=seeds)
     inner = _interior(W, H, (7, -4), 20)
     assert np.all(fwd[inner] == [56, -32])
+
+
+# --------------------------------------------------------------------------
+# Flow Fields+ schedules (Sec. 3.3, 3.4) and the two-way check (Sec. 3.7)
+# --------------------------------------------------------------------------
+def test_schedule_counts_match_the_paper():
+    g = {k: int(v) for k, v in _golden("schedules.txt").items()}
+    P = O.Params(schedule=1, scales=3)
+    for L in range(3):
+        n = P.sweeps(L)
+        assert n == g["plus_sweeps"]
+        rs = [t for t in range(n) if O.lib().ffo_schedule_rs_after(1, 4, L, t)]
+        assert len(rs) == g["plus_random_searches"]
+        wide = [t for t in range(n) if O.lib().ffo_schedule_radius_mult(1, L, t) == 2]
+        assert wide == list(range(g["plus_wide_sweeps"]))
+        assert all(O.lib().ffo_schedule_radius_mult(1, L, t) in (1, g["plus_wide_radius_factor"])
+                   for t in range(n))
+        # the 3 random searches of the wide phase follow its first 3 sweeps
+        assert [t for t in rs if t < 4] == [0, 1, 2]
+    F = O.Params(schedule=2, scales=3)
+    assert F.sweeps(0) == g["fast_finest_sweeps"]
+    assert sum(O.lib().ffo_schedule_rs_after(2, 4, 0, t) for t in range(4)) == \
+        g["fast_finest_random_searches"]
+    assert all(O.lib().ffo_schedule_radius_mult(2, 0, t) == 1 for t in range(4))
+    assert F.sweeps(1) == g["plus_sweeps"] and F.sweeps(2) == g["plus_sweeps"]
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_schedule_eval_count_closed_form(schedule):
+    W, H, S, leaf = 45, 31, 3, 8
+    pair = workloads.random_pair(seed=77, width=W, height=H)
+    P = O.Params(scales=S, iters=4, seed_leaf=leaf, schedule=schedule)
+    _, _, ev = O.match(P, pair.img1, pair.img2, 0, 0)
+    dims = [O.level_dims(W, H, L) for L in range(S)]
+    expect = leaf * dims[S - 1][0] * dims[S - 1][1]
+    for L, (WL, HL) in enumerate(dims):
+        n = P.sweeps(L)
+        rs = sum(O.lib().ffo_schedule_rs_after(schedule, 4, L, t) for t in range(n))
+        expect += n * (2 * WL * HL - WL - HL) + rs * WL * HL
+        if L < S - 1:
+            expect += dims[L + 1][0] * dims[L + 1][1]
+    assert ev == expect
+
+
+def test_plus_schedule_composes_pinned_steps_with_wide_radius():
+    # the first two sweeps of a Flow Fields+ level: sweep 0, search with 2R,
+    # sweep 1 -- built from the single-step functions pinned above
+    pair = workloads.translation_pair(seed=8, width=64, height=48)
+    W, H = pair.width, pair.height
+    P = O.Params(scales=2, iters=4, schedule=1, radius_q3=8)
+    f1 = O.features_all(pair.img1, 2)
+    f2 = O.features_all(pair.img2, 2)
+    flow, cost, _ = O.match(P, pair.img1, pair.img2, 0, 4, until_level=1, until_sweeps=0)
+    flow, cost, _ = O.sweep_level(f1[1], f2[1], W, H, 1, 0, flow, cost)
+    flow, cost, _ = O.random_search_level(f1[1], f2[1], W, H, 1, 0, 0, 16, P.seed, 4, flow, cost)
+    flow, cost, _ = O.sweep_level(f1[1], f2[1], W, H, 1, 1, flow, cost)
+    rf, rc, _ = O.match(P, pair.img1, pair.img2, 0, 4, until_level=1, until_sweeps=2)
+    # until_sweeps=2 includes the search after sweep 1, with 2R as well
+    flow, cost, _ = O.random_search_level(f1[1], f2[1], W, H, 1, 1, 0, 16, P.seed, 4, flow, cost)
+    np.testing.assert_array_equal(rf, flow)
+    np.testing.assert_array_equal(rc, cost)
+
+
+def test_two_way_filter_needs_both_backward_flows():
+    W, H = 4, 1
+    fwd = np.zeros((H, W, 2), np.int16)
+    b1 = np.zeros((H, W, 2), np.int16)
+    b2 = np.zeros((H, W, 2), np.int16)
+    b2[0, 1] = (16, 0)         # pixel 1: consistent with b1 only
+    b1[0, 2] = (0, 16)         # pixel 2: consistent with b2 only
+    b1[0, 3] = (9, 0)          # pixel 3: consistent with neither
+    b2[0, 3] = (0, 9)
+    np.testing.assert_array_equal(O.filter_mask2(fwd, b1, b2, 8)[0], [1, 0, 0, 0])
+    np.testing.assert_array_equal(O.filter_mask2(fwd, b1, b1, 8), O.filter_mask(fwd, b1, 8))
