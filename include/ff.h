@@ -49,7 +49,18 @@ typedef enum {
     FF_ESTATE = 5
 } ff_status;
 
-typedef enum { FF_FWD = 0, FF_BWD = 1 } ff_dir;
+/* FF_BWD2: a second backward flow (slot 1 -> 0) with its own random stream,
+ * for the two-way consistency check of Sec. 3.7. */
+typedef enum { FF_FWD = 0, FF_BWD = 1, FF_BWD2 = 2 } ff_dir;
+
+/* Sweep schedules per scale.
+ * FF_SCHED_BASIC (Sec. 3.1-3.2): `iters` sweeps with radius R, a random
+ *   search after each but the last.
+ * FF_SCHED_PLUS (Flow Fields+, Sec. 3.3): 4 sweeps with R+ = 2R (3 random
+ *   searches), then 8 sweeps with R (7 random searches); `iters` is unused.
+ * FF_SCHED_PLUS_FAST (Flow Fields+ Fast, Sec. 3.4): as FF_SCHED_PLUS, but
+ *   the finest scale runs only 4 sweeps with R (3 random searches). */
+typedef enum { FF_SCHED_BASIC = 0, FF_SCHED_PLUS = 1, FF_SCHED_PLUS_FAST = 2 } ff_schedule;
 
 #define FF_MAX_SCALES 8
 #define FF_MAX_LEAF 8
@@ -69,10 +80,11 @@ typedef struct {
     uint32_t seed;    /* random-search key word 0                                        */
     int max_width;    /* largest frame the context must hold, 1..4096                     */
     int max_height;
+    int schedule;     /* an ff_schedule value                                             */
 } ff_config;
 
 /* Fills the paper's defaults: patch 8, 9 coefficients, 1 channel, S = 4,
- * I = 4, R = 1 px, l = 8, stride 1, eps = 1 px, max 1024 x 1024. */
+ * I = 4, R = 1 px, l = 8, stride 1, eps = 1 px, max 1024 x 1024, basic schedule. */
 ff_status ff_config_default(ff_config *cfg);
 
 /* Creates a context on `device` and allocates all its device memory for
@@ -92,7 +104,8 @@ ff_status ff_set_stream(ff_ctx *ctx, void *cuda_stream);
  * [channels][h][pitch], pitch >= w.  1 <= w <= max_width, 1 <= h <= max_height. */
 ff_status ff_features(ff_ctx *ctx, int slot, const uint8_t *img, int w, int h, int pitch);
 
-/* Sec. 3.1-3.2: matches slot 0 -> 1 (FF_FWD) or 1 -> 0 (FF_BWD).  Both slots
+/* Sec. 3.1-3.2: matches slot 0 -> 1 (FF_FWD) or 1 -> 0 (FF_BWD, FF_BWD2).  Each
+ * direction has its own state, so the three may run on three streams.  Both slots
  * must hold features of the same size.  pair_id: random-search key word 1.
  * seeds_in: NULL (seed by the exact top-l WHT search, Eq. 1/4) or int16
  * [H_c][W_c][2] flows on the coarsest grid (H_c = ceil(h / 2^(S-1))).
@@ -116,6 +129,12 @@ ff_status ff_match_until(ff_ctx *ctx, ff_dir dir, uint32_t pair_id, const int16_
  * mask_out: uint8 [h][w]. */
 ff_status ff_filter(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_bwd,
                     uint8_t *mask_out);
+
+/* Sec. 3.7, two backward flows: mask[p] = 1 iff p passes the check of
+ * ff_filter against flow_bwd1 and against flow_bwd2 (a pixel inconsistent
+ * with either backward flow is deleted).  Same layouts as ff_filter. */
+ff_status ff_filter_2way(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_bwd1,
+                         const int16_t *flow_bwd2, uint8_t *mask_out);
 
 /* Whole pair with HOST buffers (blocking): copies both frames in (planar
  * uint8 [channels][h][w]), builds features, matches forward and backward

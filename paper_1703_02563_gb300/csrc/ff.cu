@@ -326,6 +326,34 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
 #include "ff_sweep.cuh"
 #include "ff_seed.cuh"
 
+// Sec. 3.7 with two backward flows: kept only if consistent with both
+__global__ void k_filter2(const uint32_t *__restrict__ fwd, const uint32_t *__restrict__ b1,
+                          const uint32_t *__restrict__ b2, int W, int H, int eps,
+                          uint8_t *__restrict__ mask) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H) return;
+    const int y = i / W, x = i - y * W;
+    const uint32_t f = fwd[i];
+    uint8_t m = 0;
+    if (flow_x(f) != -32768 && flow_y(f) != -32768) {
+        const int qx = x + ((flow_x(f) + 4) >> 3), qy = y + ((flow_y(f) + 4) >> 3);
+        if (qx >= 0 && qx < W && qy >= 0 && qy < H) {
+            m = 1;
+            const uint32_t bs[2] = {b1[qy * W + qx], b2[qy * W + qx]};
+            for (int j = 0; j < 2; j++) {
+                const uint32_t b = bs[j];
+                if (flow_x(b) == -32768 || flow_y(b) == -32768) {
+                    m = 0;
+                    continue;
+                }
+                const long long dx = flow_x(f) + flow_x(b), dy = flow_y(f) + flow_y(b);
+                if (!(dx * dx + dy * dy < (long long)eps * eps)) m = 0;
+            }
+        }
+    }
+    mask[i] = m;
+}
+
 // level state -> caller's flow / cost arrays
 __global__ void k_export(const uint32_t *__restrict__ flow, const int *__restrict__ cost, int N,
                          uint32_t *__restrict__ flow_out, int *__restrict__ cost_out) {
@@ -363,6 +391,7 @@ __global__ void k_filter(const uint32_t *__restrict__ fwd, const uint32_t *__res
 namespace {
 
 constexpr int kMaxIters = 64;
+constexpr int kNumDirs = 3;   // forward, backward, second backward
 constexpr int kMaxChunks = 64;
 constexpr int kTargetCtas = 8 * 152;
 constexpr int kSeedQpt = 2;
@@ -399,7 +428,7 @@ struct ff_ctx {
     uint8_t *feat[2] = {nullptr, nullptr};
     int fw[2] = {0, 0}, fh[2] = {0, 0};
     bool have[2] = {false, false};
-    DirState dir[2];
+    DirState dir[kNumDirs];
     size_t nq_cap = 0;
     size_t edge_cap = 0;
     // staging for ff_pair_host
@@ -521,6 +550,8 @@ void free_all(ff_ctx *c) {
         cudaFree(c->feat[s]);
         cudaFree(c->img_dev[s]);
         cudaFree(c->pair_flow[s]);
+    }
+    for (int s = 0; s < kNumDirs; s++) {
         DirState &d = c->dir[s];
         cudaFree(d.flow[0]);
         cudaFree(d.flow[1]);
@@ -555,6 +586,8 @@ ff_status validate_config(const ff_config *c, std::string *why) {
     if (c->seed_leaf < 1 || c->seed_leaf > FF_MAX_LEAF) return *why = "seed_leaf must be 1..8", FF_EINVAL;
     if (c->seed_stride < 1 || c->seed_stride > 64) return *why = "seed_stride must be 1..64", FF_EINVAL;
     if (c->eps_q3 < 0 || c->eps_q3 > 65535) return *why = "eps_q3 out of range", FF_EINVAL;
+    if (c->schedule < FF_SCHED_BASIC || c->schedule > FF_SCHED_PLUS_FAST)
+        return *why = "unknown schedule", FF_EINVAL;
     if (c->max_width < 1 || c->max_width > FF_MAX_DIM || c->max_height < 1 ||
         c->max_height > FF_MAX_DIM)
         return *why = "max_width/max_height must be 1..4096", FF_EINVAL;
@@ -654,6 +687,26 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
     return check_launch(c, "k_seed_merge");
 }
 
+// Sweep schedule of one level (Sec. 3.1-3.2 basic; Sec. 3.3 Flow Fields+:
+// 4 sweeps with 2R then 8 with R, a random search after every sweep of a
+// phase but its last; Sec. 3.4 Fast: the finest scale runs 4 sweeps with R).
+bool plus_level(const ff_config &cfg, int L) {
+    return cfg.schedule == FF_SCHED_PLUS || (cfg.schedule == FF_SCHED_PLUS_FAST && L > 0);
+}
+int level_sweeps(const ff_config &cfg, int L) {
+    if (plus_level(cfg, L)) return 12;
+    if (cfg.schedule == FF_SCHED_PLUS_FAST) return 4;
+    return cfg.iters;
+}
+bool search_after(const ff_config &cfg, int L, int t) {
+    const int n = level_sweeps(cfg, L);
+    if (plus_level(cfg, L)) return t != 3 && t != n - 1;
+    return t < n - 1;
+}
+int search_radius(const ff_config &cfg, int L, int t) {
+    return (plus_level(cfg, L) && t < 4) ? 2 * cfg.radius_q3 : cfg.radius_q3;
+}
+
 ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L, uint32_t *flow,
                        int *cost, int W, int H, int L, int t, uint32_t pair_id) {
     DirState &st = c->dir[d];
@@ -675,8 +728,8 @@ ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L,
     a.d = t & 3;
     a.t = t;
     a.dir = d;
-    a.do_rs = t < c->I - 1;
-    a.radius_q3 = c->cfg.radius_q3;
+    a.do_rs = search_after(c->cfg, L, t) ? 1 : 0;
+    a.radius_q3 = search_radius(c->cfg, L, t);
     a.seed = c->cfg.seed;
     a.pair_id = pair_id;
     a.epoch = ++st.epoch;
@@ -741,8 +794,10 @@ ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seed
                     int until_level, int until_sweeps, int16_t *flow_out, int32_t *cost_out) {
     ff_status s = check_pair(c);
     if (s) return s;
-    if (dir != FF_FWD && dir != FF_BWD) return fail(c, FF_EINVAL, "dir must be FF_FWD or FF_BWD");
-    if (until_level < 0 || until_level >= c->S || until_sweeps < 0 || until_sweeps > c->I)
+    if (dir != FF_FWD && dir != FF_BWD && dir != FF_BWD2)
+        return fail(c, FF_EINVAL, "dir must be FF_FWD, FF_BWD or FF_BWD2");
+    if (until_level < 0 || until_level >= c->S || until_sweeps < 0 ||
+        until_sweeps > level_sweeps(c->cfg, until_level))
         return fail(c, FF_EINVAL, "until_level/until_sweeps out of range");
     if (!flow_out) return fail(c, FF_EINVAL, "flow_out is NULL");
     if (((uintptr_t)flow_out & 3) || ((uintptr_t)cost_out & 3) || ((uintptr_t)seeds_in & 3))
@@ -790,7 +845,7 @@ ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seed
             s = check_launch(c, "k_upsample");
         }
         if (s) return s;
-        const int sweeps = (L == until_level) ? until_sweeps : c->I;
+        const int sweeps = (L == until_level) ? until_sweeps : level_sweeps(c->cfg, L);
         for (int t = 0; t < sweeps; t++) {
             s = launch_sweep(c, d, f1L, f2L, flow, cost, W, H, L, t, pair_id);
             if (s) return s;
@@ -862,6 +917,7 @@ ff_status ff_config_default(ff_config *cfg) {
     cfg->seed = 20261203u;
     cfg->max_width = 1024;
     cfg->max_height = 1024;
+    cfg->schedule = FF_SCHED_BASIC;
     return FF_OK;
 }
 
@@ -893,6 +949,10 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < 2 && e == cudaSuccess; s++) {
         e = alloc(&c->feat[s], c->feat_cap);
+        if (e == cudaSuccess) e = alloc(&c->img_dev[s], npix * c->C);
+        if (e == cudaSuccess) e = alloc(&c->pair_flow[s], npix);
+    }
+    for (int s = 0; s < kNumDirs && e == cudaSuccess; s++) {
         DirState &d = c->dir[s];
         if (e == cudaSuccess) e = alloc(&d.flow[0], npix);
         if (e == cudaSuccess) e = alloc(&d.flow[1], npix);
@@ -911,8 +971,6 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
         if (e == cudaSuccess) e = alloc(&d.cbf, npix * K);
         if (e == cudaSuccess) e = alloc(&d.err, 1);
         if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int));
-        if (e == cudaSuccess) e = alloc(&c->img_dev[s], npix * c->C);
-        if (e == cudaSuccess) e = alloc(&c->pair_flow[s], npix);
     }
     if (e == cudaSuccess) e = alloc(&c->pair_mask, npix);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
@@ -968,7 +1026,7 @@ ff_status ff_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seeds
                    int16_t *flow_out, int32_t *cost_out) {
     if (!c) return FF_EINVAL;
     DeviceGuard guard(c->device);
-    return run_match(c, dir, pair_id, seeds_in, 0, c->I, flow_out, cost_out);
+    return run_match(c, dir, pair_id, seeds_in, 0, level_sweeps(c->cfg, 0), flow_out, cost_out);
 }
 
 ff_status ff_match_until(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
@@ -996,6 +1054,24 @@ ff_status ff_filter(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd,
     return check_launch(c, "k_filter");
 }
 
+ff_status ff_filter_2way(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd1,
+                         const int16_t *flow_bwd2, uint8_t *mask_out) {
+    if (!c) return FF_EINVAL;
+    if (!flow_fwd || !flow_bwd1 || !flow_bwd2 || !mask_out)
+        return fail(c, FF_EINVAL, "NULL argument");
+    if (((uintptr_t)flow_fwd & 3) || ((uintptr_t)flow_bwd1 & 3) || ((uintptr_t)flow_bwd2 & 3))
+        return fail(c, FF_EINVAL, "flows must be 4-byte aligned");
+    ff_status s = check_pair(c);
+    if (s) return s;
+    DeviceGuard guard(c->device);
+    const int W = c->fw[0], H = c->fh[0], N = W * H;
+    prof_begin(c, "k_filter");
+    k_filter2<<<(N + 255) / 256, 256, 0, c->stream>>>(
+        (const uint32_t *)flow_fwd, (const uint32_t *)flow_bwd1, (const uint32_t *)flow_bwd2, W, H,
+        c->cfg.eps_q3, mask_out);
+    return check_launch(c, "k_filter");
+}
+
 ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_host, int w,
                        int h, uint32_t pair_id, int16_t *flow_fwd_host, int16_t *flow_bwd_host,
                        uint8_t *mask_host) {
@@ -1019,10 +1095,12 @@ ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_
     if ((s = check_cuda(c, cudaEventRecord(c->ev_a, main), "event"))) return s;
     if ((s = check_cuda(c, cudaStreamWaitEvent(c->side, c->ev_a, 0), "wait"))) return s;
     c->stream = c->side;
-    s = run_match(c, FF_BWD, pair_id, nullptr, 0, c->I, (int16_t *)c->pair_flow[1], nullptr);
+    s = run_match(c, FF_BWD, pair_id, nullptr, 0, level_sweeps(c->cfg, 0),
+                  (int16_t *)c->pair_flow[1], nullptr);
     c->stream = main;
     if (s) return s;
-    if ((s = run_match(c, FF_FWD, pair_id, nullptr, 0, c->I, (int16_t *)c->pair_flow[0], nullptr)))
+    if ((s = run_match(c, FF_FWD, pair_id, nullptr, 0, level_sweeps(c->cfg, 0),
+                       (int16_t *)c->pair_flow[0], nullptr)))
         return s;
     if ((s = check_cuda(c, cudaEventRecord(c->ev_b, c->side), "event"))) return s;
     if ((s = check_cuda(c, cudaStreamWaitEvent(main, c->ev_b, 0), "wait"))) return s;
@@ -1042,14 +1120,13 @@ ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_
                                            main), "copy mask")))
         return s;
     if ((s = check_cuda(c, cudaStreamSynchronize(main), "synchronize"))) return s;
-    int err[2] = {0, 0};
-    for (int d = 0; d < 2; d++)
+    int err[kNumDirs] = {0, 0, 0};
+    for (int d = 0; d < kNumDirs; d++)
         if ((s = check_cuda(c, cudaMemcpy(&err[d], c->dir[d].err, sizeof(int),
                                           cudaMemcpyDeviceToHost), "read error word")))
             return s;
-    if (err[0] || err[1]) {
-        cudaMemset(c->dir[0].err, 0, sizeof(int));
-        cudaMemset(c->dir[1].err, 0, sizeof(int));
+    if (err[0] || err[1] || err[2]) {
+        for (int d = 0; d < kNumDirs; d++) cudaMemset(c->dir[d].err, 0, sizeof(int));
         return fail(c, FF_ETIMEOUT, "a bounded device wait expired during matching");
     }
     return FF_OK;
@@ -1078,7 +1155,8 @@ ff_status ff_seed_knn(ff_ctx *c, ff_dir dir, int32_t *idx_out, int32_t *dist_out
     if (!c) return FF_EINVAL;
     ff_status s = check_pair(c);
     if (s) return s;
-    if (dir != FF_FWD && dir != FF_BWD) return fail(c, FF_EINVAL, "dir must be FF_FWD or FF_BWD");
+    if (dir != FF_FWD && dir != FF_BWD && dir != FF_BWD2)
+        return fail(c, FF_EINVAL, "dir must be FF_FWD, FF_BWD or FF_BWD2");
     if (!idx_out || !dist_out) return fail(c, FF_EINVAL, "NULL output");
     DeviceGuard guard(c->device);
     const int d = (int)dir, W = c->fw[0], H = c->fh[0];
@@ -1155,15 +1233,14 @@ ff_status ff_sync(ff_ctx *c) {
     DeviceGuard guard(c->device);
     ff_status s = check_cuda(c, cudaDeviceSynchronize(), "synchronize");
     if (s) return s;
-    int err[2] = {0, 0};
-    for (int d = 0; d < 2; d++) {
+    int err[kNumDirs] = {0, 0, 0};
+    for (int d = 0; d < kNumDirs; d++) {
         s = check_cuda(c, cudaMemcpy(&err[d], c->dir[d].err, sizeof(int), cudaMemcpyDeviceToHost),
                        "read error word");
         if (s) return s;
     }
-    if (err[0] || err[1]) {
-        cudaMemset(c->dir[0].err, 0, sizeof(int));
-        cudaMemset(c->dir[1].err, 0, sizeof(int));
+    if (err[0] || err[1] || err[2]) {
+        for (int d = 0; d < kNumDirs; d++) cudaMemset(c->dir[d].err, 0, sizeof(int));
         cudaDeviceSynchronize();
         return fail(c, FF_ETIMEOUT, "a bounded device wait expired during matching");
     }

@@ -16,12 +16,13 @@ from dataclasses import dataclass
 from . import _build
 
 FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_ETIMEOUT, FF_ESTATE = range(6)
-FF_FWD, FF_BWD = 0, 1
+FF_FWD, FF_BWD, FF_BWD2 = 0, 1, 2
+FF_SCHED_BASIC, FF_SCHED_PLUS, FF_SCHED_PLUS_FAST = 0, 1, 2
 FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS = 1, 2, 3
 INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
-            "ff_match_until", "ff_filter", "ff_pair_host", "ff_get_features", "ff_seed_knn",
+            "ff_match_until", "ff_filter", "ff_filter_2way", "ff_pair_host", "ff_get_features", "ff_seed_knn",
             "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
             "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy")
 
@@ -30,7 +31,8 @@ class ff_config(ct.Structure):
     _fields_ = [("patch", ct.c_int), ("n_coeffs", ct.c_int), ("channels", ct.c_int),
                 ("scales", ct.c_int), ("iters", ct.c_int), ("radius_q3", ct.c_int),
                 ("seed_leaf", ct.c_int), ("seed_stride", ct.c_int), ("eps_q3", ct.c_int),
-                ("seed", ct.c_uint32), ("max_width", ct.c_int), ("max_height", ct.c_int)]
+                ("seed", ct.c_uint32), ("max_width", ct.c_int), ("max_height", ct.c_int),
+                ("schedule", ct.c_int)]
 
 
 class FFError(RuntimeError):
@@ -56,6 +58,7 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_match.argtypes = [P, i, u32, P, P, P]
         L.ff_match_until.argtypes = [P, i, u32, P, i, i, P, P]
         L.ff_filter.argtypes = [P, P, P, P]
+        L.ff_filter_2way.argtypes = [P, P, P, P, P]
         L.ff_pair_host.argtypes = [P, P, P, i, i, u32, P, P, P]
         L.ff_get_features.argtypes = [P, i, i, P]
         L.ff_seed_knn.argtypes = [P, i, P, P]
@@ -121,6 +124,14 @@ class Config:
     max_height: int = 1024
     patch: int = 8
     n_coeffs: int = 9
+    schedule: int = FF_SCHED_BASIC
+
+    def sweeps(self, level: int) -> int:
+        """Sweeps of `level` under this config's schedule."""
+        plus = self.schedule == FF_SCHED_PLUS or (self.schedule == FF_SCHED_PLUS_FAST and level > 0)
+        if plus:
+            return 12
+        return 4 if self.schedule == FF_SCHED_PLUS_FAST else self.iters
 
     def c(self) -> ff_config:
         c = ff_config()
@@ -170,6 +181,11 @@ def ff_match_until(ctx: int, direction: int, pair_id: int, seeds_in, until_level
 
 def ff_filter(ctx: int, flow_fwd, flow_bwd, mask_out) -> None:
     _check(ctx, lib().ff_filter(ctx, _ptr(flow_fwd), _ptr(flow_bwd), _ptr(mask_out)))
+
+
+def ff_filter_2way(ctx: int, flow_fwd, flow_bwd1, flow_bwd2, mask_out) -> None:
+    _check(ctx, lib().ff_filter_2way(ctx, _ptr(flow_fwd), _ptr(flow_bwd1), _ptr(flow_bwd2),
+                                     _ptr(mask_out)))
 
 
 def ff_pair_host(ctx: int, img1_host, img2_host, w: int, h: int, pair_id: int,
@@ -278,12 +294,12 @@ class Context:
         torch = self.torch
         W, H = self.size
         if until_sweeps is None:
-            until_sweeps = self.cfg.iters
+            until_sweeps = self.cfg.sweeps(until_level)
         WL, HL = level_dims(W, H, until_level)
         dev = torch.device("cuda", self.device)
         flow = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
         cost = torch.empty((HL, WL), dtype=torch.int32, device=dev) if with_cost else None
-        if until_level == 0 and until_sweeps == self.cfg.iters:
+        if until_level == 0 and until_sweeps == self.cfg.sweeps(0):
             ff_match(self.ctx, direction, pair_id, seeds_in, flow, cost)
         else:
             ff_match_until(self.ctx, direction, pair_id, seeds_in, until_level, until_sweeps,
@@ -295,6 +311,13 @@ class Context:
         W, H = self.size
         mask = torch.empty((H, W), dtype=torch.uint8, device=flow_fwd.device)
         ff_filter(self.ctx, flow_fwd, flow_bwd, mask)
+        return mask
+
+    def filter_2way(self, flow_fwd, flow_bwd1, flow_bwd2):
+        torch = self.torch
+        W, H = self.size
+        mask = torch.empty((H, W), dtype=torch.uint8, device=flow_fwd.device)
+        ff_filter_2way(self.ctx, flow_fwd, flow_bwd1, flow_bwd2, mask)
         return mask
 
     def features_of(self, slot: int, level: int):
