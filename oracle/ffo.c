@@ -281,21 +281,30 @@ int ffo_seed_knn_rows(const int8_t *f1_0, const int8_t *f2_0, int C, int W, int 
  * Flow Fields+ (Sec. 3.3): 4 sweeps with R+ = 2R (3 random searches), then 8
  *   sweeps with R (7 random searches); the four directions repeat every 4.
  * Flow Fields+ Fast (Sec. 3.4): as Flow Fields+, but the finest scale runs
- *   only 4 sweeps with R (3 random searches). */
+ *   only 4 sweeps with R (3 random searches).
+ * Flow Fields+ Fast x2 (Sec. 3.4): the finest scale is not run at all (its
+ *   matches are the 2nd-finest scale's, one per 2x2 region); the 2nd-finest
+ *   runs 4 sweeps with R, the coarser ones 4 with R+ and 8 with R. */
+static int plus_level(int schedule, int L) {
+    return schedule == 1 || (schedule == 2 && L > 0) || (schedule == 3 && L > 1);
+}
+
+int ffo_schedule_final_level(int schedule) { return schedule == 3 ? 1 : 0; }
+
 int ffo_schedule_sweeps(int schedule, int iters, int L) {
-    if (schedule == 1) return 12;
-    if (schedule == 2) return L == 0 ? 4 : 12;
+    if (plus_level(schedule, L)) return 12;
+    if (L < ffo_schedule_final_level(schedule)) return 0;
+    if (schedule == 2 || schedule == 3) return 4;
     return iters;
 }
 
 int ffo_schedule_radius_mult(int schedule, int L, int t) {
-    if (schedule == 1 || (schedule == 2 && L > 0)) return t < 4 ? 2 : 1;
-    return 1;
+    return (plus_level(schedule, L) && t < 4) ? 2 : 1;
 }
 
 int ffo_schedule_rs_after(int schedule, int iters, int L, int t) {
     const int n = ffo_schedule_sweeps(schedule, iters, L);
-    if (schedule == 1 || (schedule == 2 && L > 0)) return t != 3 && t != n - 1;
+    if (plus_level(schedule, L)) return t != 3 && t != n - 1;
     return t < n - 1;
 }
 
@@ -460,7 +469,8 @@ int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *
     int C = prm->channels, S = prm->scales, I = prm->iters, sch = prm->schedule;
     if (W < 1 || H < 1 || W > 4096 || H > 4096 || (C != 1 && C != 3) || S < 1 || S > 8 ||
         I < 1 || prm->seed_leaf < 1 || prm->seed_stride < 1 || prm->radius_q3 < 0 ||
-        sch < 0 || sch > 2 || until_level < 0 || until_level >= S || until_sweeps < 0 ||
+        sch < 0 || sch > 3 || until_level < ffo_schedule_final_level(sch) ||
+        until_level >= S || until_sweeps < 0 ||
         until_sweeps > ffo_schedule_sweeps(sch, I, until_level))
         return 1;
     int64_t evals = 0;
@@ -584,19 +594,23 @@ int ffo_match(const ffo_params *prm, const uint8_t *src, const uint8_t *dst, int
 }
 
 /* Sec. 3.7: keep p iff |F(p) + F_b(p + F(p))| < eps.  Reading: F_b is read at
- * the nearest pixel to p + F(p) (rounded half up); a target outside the image
- * or an INVALID flow rejects the pixel. */
-void ffo_filter(const int16_t *fwd, const int16_t *bwd, int W, int H, int eps_q3,
-                uint8_t *mask) {
-    for (int y = 0; y < H; y++)
-        for (int x = 0; x < W; x++) {
-            long i = (long)y * W + x;
+ * the nearest point of the flows' grid to p + F(p) (rounded half up); a
+ * target outside the grid or an INVALID flow rejects the point.  The grid is
+ * the pixel grid, or the level-L grid (points (x n, y n), n = 2^L) for flows
+ * that end on a coarser scale (Fast x2, Sec. 3.4). */
+void ffo_filter_grid(const int16_t *fwd, const int16_t *bwd, int WL, int HL, int L, int eps_q3,
+                     uint8_t *mask) {
+    const int n = 1 << L;
+    for (int y = 0; y < HL; y++)
+        for (int x = 0; x < WL; x++) {
+            long i = (long)y * WL + x;
             int Fx = fwd[2 * i], Fy = fwd[2 * i + 1];
             mask[i] = 0;
             if (Fx == INVALID_F || Fy == INVALID_F) continue;
-            int qx = x + floor_div(Fx + 4, 8), qy = y + floor_div(Fy + 4, 8);
-            if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
-            long j = (long)qy * W + qx;
+            /* nearest grid point to (x n + Fx / 8) / n */
+            int qx = x + floor_div(Fx + 4 * n, 8 * n), qy = y + floor_div(Fy + 4 * n, 8 * n);
+            if (qx < 0 || qx >= WL || qy < 0 || qy >= HL) continue;
+            long j = (long)qy * WL + qx;
             int Bx = bwd[2 * j], By = bwd[2 * j + 1];
             if (Bx == INVALID_F || By == INVALID_F) continue;
             long ddx = Fx + Bx, ddy = Fy + By;
@@ -604,14 +618,19 @@ void ffo_filter(const int16_t *fwd, const int16_t *bwd, int W, int H, int eps_q3
         }
 }
 
+void ffo_filter(const int16_t *fwd, const int16_t *bwd, int W, int H, int eps_q3,
+                uint8_t *mask) {
+    ffo_filter_grid(fwd, bwd, W, H, 0, eps_q3, mask);
+}
+
 /* Sec. 3.7: with two backward flows (different random streams), a pixel is
  * deleted if it is not consistent with either of them. */
-void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, int W, int H,
-                 int eps_q3, uint8_t *mask) {
-    long n = (long)W * H;
+void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, int WL, int HL,
+                 int L, int eps_q3, uint8_t *mask) {
+    long n = (long)WL * HL;
     uint8_t *m2 = (uint8_t *)malloc((size_t)n);
-    ffo_filter(fwd, bwd1, W, H, eps_q3, mask);
-    ffo_filter(fwd, bwd2, W, H, eps_q3, m2);
+    ffo_filter_grid(fwd, bwd1, WL, HL, L, eps_q3, mask);
+    ffo_filter_grid(fwd, bwd2, WL, HL, L, eps_q3, m2);
     for (long i = 0; i < n; i++) mask[i] = (uint8_t)(mask[i] & m2[i]);
     free(m2);
 }

@@ -35,13 +35,15 @@ typedef struct {
     int seed_leaf;    /* l: candidates kept by the seeding search  */
     int seed_stride;  /* sigma: candidate grid stride in image 2   */
     uint32_t seed;    /* Philox key word 0                         */
-    int schedule;     /* 0 basic, 1 Flow Fields+, 2 Flow Fields+ Fast */
+    int schedule;     /* 0 basic, 1 Flow Fields+, 2 Flow Fields+ Fast, 3 Fast x2 */
 } ffo_params;
 
 /* The sweep schedule of one level: number of sweeps, and for sweep t the
  * random-search radius multiplier (1 or 2) and whether a random search
  * follows it. */
 int ffo_schedule_sweeps(int schedule, int iters, int L);
+/* the finest level a schedule runs (1 for Fast x2, else 0) */
+int ffo_schedule_final_level(int schedule);
 int ffo_schedule_radius_mult(int schedule, int L, int t);
 int ffo_schedule_rs_after(int schedule, int iters, int L, int t);
 
@@ -115,9 +117,13 @@ int ffo_match(const ffo_params *prm, const uint8_t *src, const uint8_t *dst, int
 /* forward/backward consistency check: mask 1 keeps a pixel */
 void ffo_filter(const int16_t *fwd, const int16_t *bwd, int W, int H, int eps_q3,
                 uint8_t *mask);
-/* two backward flows: a pixel is kept only if consistent with both */
-void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, int W, int H,
-                 int eps_q3, uint8_t *mask);
+/* the same on the level-L grid [HL][WL] (points (x 2^L, y 2^L)) */
+void ffo_filter_grid(const int16_t *fwd, const int16_t *bwd, int WL, int HL, int L, int eps_q3,
+                     uint8_t *mask);
+/* two backward flows on the level-L grid: a point is kept only if consistent
+ * with both */
+void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, int WL, int HL,
+                 int L, int eps_q3, uint8_t *mask);
 
 #ifdef __cplusplus
 }

@@ -49,7 +49,10 @@ def lib():
         L.ffo_match.argtypes = [P, P, P, i, i, i, ct.c_uint32, P, i, i, P, P, P]
         L.ffo_match.restype = i
         L.ffo_filter.argtypes = [P, P, i, i, i, P]
-        L.ffo_filter2.argtypes = [P, P, P, i, i, i, P]
+        L.ffo_filter_grid.argtypes = [P, P, i, i, i, i, P]
+        L.ffo_filter2.argtypes = [P, P, P, i, i, i, i, P]
+        L.ffo_schedule_final_level.argtypes = [i]
+        L.ffo_schedule_final_level.restype = i
         L.ffo_schedule_sweeps.argtypes = [i, i, i]
         L.ffo_schedule_sweeps.restype = i
         L.ffo_schedule_radius_mult.argtypes = [i, i, i]
@@ -78,7 +81,7 @@ class Params:
     seed_leaf: int = 8
     seed_stride: int = 1
     seed: int = 20261203
-    schedule: int = 0   # 0 basic, 1 Flow Fields+, 2 Flow Fields+ Fast
+    schedule: int = 0   # 0 basic, 1 Flow Fields+, 2 Flow Fields+ Fast, 3 Fast x2
 
     def c(self) -> _Params:
         return _Params(self.channels, self.scales, self.iters, self.radius_q3,
@@ -86,6 +89,9 @@ class Params:
 
     def sweeps(self, level: int) -> int:
         return int(lib().ffo_schedule_sweeps(self.schedule, self.iters, level))
+
+    def final_level(self) -> int:
+        return int(lib().ffo_schedule_final_level(self.schedule))
 
 
 def _p(a: np.ndarray):
@@ -197,8 +203,10 @@ def seed_knn_rows(f1_0: np.ndarray, f2_0: np.ndarray, S: int, gy0: int, gy1: int
 
 def match_features(prm: Params, fsrc: list[np.ndarray], fdst: list[np.ndarray], W: int, H: int,
                    direction: int = 0, pair_id: int = 0, seeds_in: np.ndarray | None = None,
-                   until_level: int = 0, until_sweeps: int | None = None):
+                   until_level: int | None = None, until_sweeps: int | None = None):
     """Returns (flow int16 [HL][WL][2], cost int32 [HL][WL], evals)."""
+    if until_level is None:
+        until_level = prm.final_level()
     if until_sweeps is None:
         until_sweeps = prm.sweeps(until_level)
     WL, HL = level_dims(W, H, until_level)
@@ -219,13 +227,15 @@ def match_features(prm: Params, fsrc: list[np.ndarray], fdst: list[np.ndarray], 
 
 
 def match(prm: Params, src: np.ndarray, dst: np.ndarray, direction: int = 0, pair_id: int = 0,
-          seeds_in: np.ndarray | None = None, until_level: int = 0,
+          seeds_in: np.ndarray | None = None, until_level: int | None = None,
           until_sweeps: int | None = None):
     """Match image src -> dst.  Returns (flow, cost, evals) at the stop level."""
     src = np.ascontiguousarray(src, np.uint8)
     dst = np.ascontiguousarray(dst, np.uint8)
     C, H, W = src.shape
     assert C == prm.channels and dst.shape == src.shape
+    if until_level is None:
+        until_level = prm.final_level()
     if until_sweeps is None:
         until_sweeps = prm.sweeps(until_level)
     WL, HL = level_dims(W, H, until_level)
@@ -244,12 +254,16 @@ def match(prm: Params, src: np.ndarray, dst: np.ndarray, direction: int = 0, pai
     return flow, cst, ev.value
 
 
-def filter_mask(fwd: np.ndarray, bwd: np.ndarray, eps_q3: int) -> np.ndarray:
+def filter_mask(fwd: np.ndarray, bwd: np.ndarray, eps_q3: int, level: int = 0) -> np.ndarray:
+    """Consistency mask of flows on the level-`level` grid (0: pixels)."""
     fwd = np.ascontiguousarray(fwd, np.int16)
     bwd = np.ascontiguousarray(bwd, np.int16)
     H, W, _ = fwd.shape
     mask = np.zeros((H, W), np.uint8)
-    lib().ffo_filter(_p(fwd), _p(bwd), W, H, eps_q3, _p(mask))
+    if level == 0:
+        lib().ffo_filter(_p(fwd), _p(bwd), W, H, eps_q3, _p(mask))
+    else:
+        lib().ffo_filter_grid(_p(fwd), _p(bwd), W, H, level, eps_q3, _p(mask))
     return mask
 
 
@@ -278,12 +292,13 @@ def random_search_level(f1L, f2L, W: int, H: int, L: int, t: int, direction: int
     return flow, cost, ev.value
 
 
-def filter_mask2(fwd: np.ndarray, bwd1: np.ndarray, bwd2: np.ndarray, eps_q3: int) -> np.ndarray:
+def filter_mask2(fwd: np.ndarray, bwd1: np.ndarray, bwd2: np.ndarray, eps_q3: int,
+                 level: int = 0) -> np.ndarray:
     """Two-way check: consistent with both backward flows."""
     fwd = np.ascontiguousarray(fwd, np.int16)
     bwd1 = np.ascontiguousarray(bwd1, np.int16)
     bwd2 = np.ascontiguousarray(bwd2, np.int16)
     H, W, _ = fwd.shape
     mask = np.zeros((H, W), np.uint8)
-    lib().ffo_filter2(_p(fwd), _p(bwd1), _p(bwd2), W, H, eps_q3, _p(mask))
+    lib().ffo_filter2(_p(fwd), _p(bwd1), _p(bwd2), W, H, level, eps_q3, _p(mask))
     return mask

@@ -542,7 +542,25 @@ def test_schedule_counts_match_the_paper():
     assert F.sweeps(1) == g["plus_sweeps"] and F.sweeps(2) == g["plus_sweeps"]
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+def test_fast_x2_schedule_counts_match_the_paper():
+    g = {k: int(v) for k, v in _golden("schedules.txt").items()}
+    X = O.Params(schedule=3, scales=4)
+    assert X.final_level() == g["x2_final_level"]
+    assert 1 << X.final_level() == g["x2_match_region"]
+    assert X.sweeps(0) == g["x2_finest_sweeps"]
+    assert X.sweeps(1) == g["x2_second_sweeps"]
+    assert sum(O.lib().ffo_schedule_rs_after(3, 4, 1, t) for t in range(4)) == \
+        g["x2_second_random_searches"]
+    assert all(O.lib().ffo_schedule_radius_mult(3, 1, t) == 1 for t in range(4))
+    for L in (2, 3):
+        assert X.sweeps(L) == g["plus_sweeps"]
+        assert [O.lib().ffo_schedule_radius_mult(3, L, t) for t in range(12)] == \
+            [O.lib().ffo_schedule_radius_mult(1, L, t) for t in range(12)]
+    for sch in (0, 1, 2):
+        assert O.Params(schedule=sch).final_level() == 0
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_schedule_eval_count_closed_form(schedule):
     W, H, S, leaf = 45, 31, 3, 8
     pair = workloads.random_pair(seed=77, width=W, height=H)
@@ -551,6 +569,8 @@ def test_schedule_eval_count_closed_form(schedule):
     dims = [O.level_dims(W, H, L) for L in range(S)]
     expect = leaf * dims[S - 1][0] * dims[S - 1][1]
     for L, (WL, HL) in enumerate(dims):
+        if L < P.final_level():
+            continue
         n = P.sweeps(L)
         rs = sum(O.lib().ffo_schedule_rs_after(schedule, 4, L, t) for t in range(n))
         expect += n * (2 * WL * HL - WL - HL) + rs * WL * HL
@@ -589,3 +609,63 @@ def test_two_way_filter_needs_both_backward_flows():
     b2[0, 3] = (0, 9)
     np.testing.assert_array_equal(O.filter_mask2(fwd, b1, b2, 8)[0], [1, 0, 0, 0])
     np.testing.assert_array_equal(O.filter_mask2(fwd, b1, b1, 8), O.filter_mask(fwd, b1, 8))
+
+
+def test_fast_x2_is_flow_fields_plus_cut_short_at_the_second_scale():
+    # coarser scales run exactly as Flow Fields+; the 2nd-finest scale is the
+    # upsampled state followed by 4 sweeps with R and 3 random searches, made
+    # of the single-step functions pinned above; the finest never runs
+    pair = workloads.layered_pair(seed=5, width=72, height=52, channels=3, max_disp=10)
+    W, H, S = pair.width, pair.height, 3
+    X = O.Params(channels=3, scales=S, schedule=3, radius_q3=8, seed_stride=2)
+    Pp = O.Params(channels=3, scales=S, schedule=1, radius_q3=8, seed_stride=2)
+    for k in (0, 5, 12):
+        a = O.match(X, pair.img1, pair.img2, 0, 3, until_level=2, until_sweeps=k)
+        b = O.match(Pp, pair.img1, pair.img2, 0, 3, until_level=2, until_sweeps=k)
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+    f1 = O.features_all(pair.img1, S)
+    f2 = O.features_all(pair.img2, S)
+    flow, cost, _ = O.match(X, pair.img1, pair.img2, 0, 3, until_level=1, until_sweeps=0)
+    for t in range(4):
+        flow, cost, _ = O.sweep_level(f1[1], f2[1], W, H, 1, t, flow, cost)
+        if t < 3:
+            flow, cost, _ = O.random_search_level(f1[1], f2[1], W, H, 1, t, 0, 8, X.seed, 3,
+                                                  flow, cost)
+    rf, rc, _ = O.match(X, pair.img1, pair.img2, 0, 3)
+    assert rf.shape[:2] == O.level_dims(W, H, 1)[::-1]
+    np.testing.assert_array_equal(rf, flow)
+    np.testing.assert_array_equal(rc, cost)
+    with pytest.raises(ValueError):
+        O.match(X, pair.img1, pair.img2, 0, 3, until_level=0, until_sweeps=0)
+
+
+def test_grid_filter_worked_example():
+    # level-1 grid: point (x 2, y 2); a forward flow of exactly 1 px lies half
+    # way between grid points 0 and 1 and rounds up to grid point 1
+    fwd = np.zeros((1, 4, 2), np.int16)
+    bwd = np.zeros((1, 4, 2), np.int16)
+    fwd[0, 0] = (8, 0)      # -> grid 1, bwd there (-8, 0): consistent
+    fwd[0, 1] = (4, 0)      # -> grid 1 (itself), bwd (-8, 0): |(-4, 0)| < 1 px
+    fwd[0, 2] = (-9, 0)     # -> grid 1 (2*2*8 - 9 = 23 Q3 -> 1.44 grid), bwd (-8,0): far
+    fwd[0, 3] = (8, 0)      # -> grid 4: outside
+    bwd[0, 1] = (-8, 0)
+    bwd[0, 2] = (9, 0)
+    np.testing.assert_array_equal(O.filter_mask(fwd, bwd, 8, level=1)[0], [1, 1, 0, 0])
+    # on the pixel grid point 1 reads pixel 2, whose (9, 0) is inconsistent
+    np.testing.assert_array_equal(O.filter_mask(fwd, bwd, 8, level=0)[0], [1, 0, 0, 0])
+
+
+def test_grid_filter_is_the_pixel_filter_on_block_constant_flows():
+    # flows constant on 2x2 blocks with whole 2-px displacements land on even
+    # pixels, so the level-1 check is the pixel check subsampled
+    rng = np.random.default_rng(4)
+    W, H = 30, 22
+    blocks = lambda a: np.repeat(np.repeat(a, 2, axis=0), 2, axis=1)[:H, :W]
+    fwd = blocks(16 * rng.integers(-3, 4, (H // 2, W // 2, 2))).astype(np.int16)
+    bwd = blocks(16 * rng.integers(-3, 4, (H // 2, W // 2, 2))).astype(np.int16)
+    bwd[fwd[..., 0] > 16] = -fwd[fwd[..., 0] > 16]
+    full = O.filter_mask(fwd, bwd, 12)
+    grid = O.filter_mask(fwd[::2, ::2], bwd[::2, ::2], 12, level=1)
+    assert 0 < grid.sum() < grid.size
+    np.testing.assert_array_equal(grid, full[::2, ::2])
