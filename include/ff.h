@@ -59,8 +59,19 @@ typedef enum { FF_FWD = 0, FF_BWD = 1, FF_BWD2 = 2 } ff_dir;
  * FF_SCHED_PLUS (Flow Fields+, Sec. 3.3): 4 sweeps with R+ = 2R (3 random
  *   searches), then 8 sweeps with R (7 random searches); `iters` is unused.
  * FF_SCHED_PLUS_FAST (Flow Fields+ Fast, Sec. 3.4): as FF_SCHED_PLUS, but
- *   the finest scale runs only 4 sweeps with R (3 random searches). */
-typedef enum { FF_SCHED_BASIC = 0, FF_SCHED_PLUS = 1, FF_SCHED_PLUS_FAST = 2 } ff_schedule;
+ *   the finest scale runs only 4 sweeps with R (3 random searches).
+ * FF_SCHED_PLUS_FAST_X2 (Flow Fields+ Fast x2, Sec. 3.4): the finest scale
+ *   is not run; the 2nd-finest runs 4 sweeps with R and the coarser ones as
+ *   FF_SCHED_PLUS.  Matches come on the level-1 grid, one per 2x2 region:
+ *   the "final grid" below is [ceil(H/2)][ceil(W/2)] (points (2x, 2y)) for
+ *   this schedule and the pixel grid [H][W] for the others.  The paper pairs
+ *   it with seed_stride = 2.  Needs scales >= 2. */
+typedef enum {
+    FF_SCHED_BASIC = 0,
+    FF_SCHED_PLUS = 1,
+    FF_SCHED_PLUS_FAST = 2,
+    FF_SCHED_PLUS_FAST_X2 = 3
+} ff_schedule;
 
 #define FF_MAX_SCALES 8
 #define FF_MAX_LEAF 8
@@ -109,7 +120,8 @@ ff_status ff_features(ff_ctx *ctx, int slot, const uint8_t *img, int w, int h, i
  * must hold features of the same size.  pair_id: random-search key word 1.
  * seeds_in: NULL (seed by the exact top-l WHT search, Eq. 1/4) or int16
  * [H_c][W_c][2] flows on the coarsest grid (H_c = ceil(h / 2^(S-1))).
- * flow_out: int16 [h][w][2]; cost_out: int32 [h][w] or NULL.  Both 4-byte
+ * flow_out: int16 [h][w][2]; cost_out: int32 [h][w] or NULL (the final grid
+ * of the schedule: [ceil(h/2)][ceil(w/2)] for Fast x2).  Both 4-byte
  * aligned. */
 ff_status ff_match(ff_ctx *ctx, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
                    int16_t *flow_out, int32_t *cost_out);
@@ -118,15 +130,17 @@ ff_status ff_match(ff_ctx *ctx, ff_dir dir, uint32_t pair_id, const int16_t *see
  * (each followed by its random search when one follows it) and writes that
  * level's grid: flow_out int16 [H_L][W_L][2], cost_out int32 [H_L][W_L].
  * until_sweeps = 0 returns the level's initial state (seeds or upsampled
- * flows).  Used to check each stage of the method. */
+ * flows).  until_level >= 1 under Fast x2.  Used to check each stage of the
+ * method. */
 ff_status ff_match_until(ff_ctx *ctx, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
                          int until_level, int until_sweeps, int16_t *flow_out,
                          int32_t *cost_out);
 
-/* Sec. 3.7: mask[p] = 1 iff |F(p) + F_b(q)| < eps, q = the pixel nearest to
- * p + F(p) (rounded half up); 0 when q is outside the frame or a flow is
- * unset.  flow_fwd / flow_bwd: int16 [h][w][2] of the last ff_features size;
- * mask_out: uint8 [h][w]. */
+/* Sec. 3.7: mask[p] = 1 iff |F(p) + F_b(q)| < eps, q = the point of the
+ * final grid nearest to p + F(p) (rounded half up); 0 when q is outside the
+ * grid or a flow is unset.  flow_fwd / flow_bwd: int16 [h][w][2] of the last
+ * ff_features size ([ceil(h/2)][ceil(w/2)][2] for Fast x2); mask_out: uint8
+ * of the same grid. */
 ff_status ff_filter(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_bwd,
                     uint8_t *mask_out);
 
@@ -139,8 +153,8 @@ ff_status ff_filter_2way(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *fl
 /* Whole pair with HOST buffers (blocking): copies both frames in (planar
  * uint8 [channels][h][w]), builds features, matches forward and backward
  * concurrently, filters, and copies the results out: flow_fwd_host and
- * flow_bwd_host int16 [h][w][2], mask_host uint8 [h][w] (any may be NULL to
- * skip its copy).  Pinned host memory makes the copies asynchronous.
+ * flow_bwd_host int16 [h][w][2], mask_host uint8 [h][w] (on the final grid
+ * of the schedule; any may be NULL to skip its copy).  Pinned host memory makes the copies asynchronous.
  * Returns after the results are on the host. */
 ff_status ff_pair_host(ff_ctx *ctx, const uint8_t *img1_host, const uint8_t *img2_host,
                        int w, int h, uint32_t pair_id, int16_t *flow_fwd_host,

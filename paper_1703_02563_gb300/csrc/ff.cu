@@ -326,34 +326,6 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
 #include "ff_sweep.cuh"
 #include "ff_seed.cuh"
 
-// Sec. 3.7 with two backward flows: kept only if consistent with both
-__global__ void k_filter2(const uint32_t *__restrict__ fwd, const uint32_t *__restrict__ b1,
-                          const uint32_t *__restrict__ b2, int W, int H, int eps,
-                          uint8_t *__restrict__ mask) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= W * H) return;
-    const int y = i / W, x = i - y * W;
-    const uint32_t f = fwd[i];
-    uint8_t m = 0;
-    if (flow_x(f) != -32768 && flow_y(f) != -32768) {
-        const int qx = x + ((flow_x(f) + 4) >> 3), qy = y + ((flow_y(f) + 4) >> 3);
-        if (qx >= 0 && qx < W && qy >= 0 && qy < H) {
-            m = 1;
-            const uint32_t bs[2] = {b1[qy * W + qx], b2[qy * W + qx]};
-            for (int j = 0; j < 2; j++) {
-                const uint32_t b = bs[j];
-                if (flow_x(b) == -32768 || flow_y(b) == -32768) {
-                    m = 0;
-                    continue;
-                }
-                const long long dx = flow_x(f) + flow_x(b), dy = flow_y(f) + flow_y(b);
-                if (!(dx * dx + dy * dy < (long long)eps * eps)) m = 0;
-            }
-        }
-    }
-    mask[i] = m;
-}
-
 // level state -> caller's flow / cost arrays
 __global__ void k_export(const uint32_t *__restrict__ flow, const int *__restrict__ cost, int N,
                          uint32_t *__restrict__ flow_out, int *__restrict__ cost_out) {
@@ -364,21 +336,32 @@ __global__ void k_export(const uint32_t *__restrict__ flow, const int *__restric
 }
 
 // Sec. 3.7 forward/backward consistency: keep p iff |F(p) + F_b(q)|^2 < eps^2
-// with q the pixel nearest to p + F(p) (half up) inside the frame.
-__global__ void k_filter(const uint32_t *__restrict__ fwd, const uint32_t *__restrict__ bwd,
-                         int W, int H, int eps, uint8_t *__restrict__ mask) {
+// Sec. 3.7 on the final grid (points (x 2^L, y 2^L)): keep p iff
+// |F(p) + F_b(q)| < eps for each of the NB backward flows, q the grid point
+// nearest to p + F(p) (half up); an INVALID flow or a q off the grid rejects p.
+template <int NB>
+__global__ void k_filter(const uint32_t *__restrict__ fwd, const uint32_t *__restrict__ b1,
+                         const uint32_t *__restrict__ b2, int W, int H, int L, int eps,
+                         uint8_t *__restrict__ mask) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= W * H) return;
     const int y = i / W, x = i - y * W;
     const uint32_t f = fwd[i];
     uint8_t m = 0;
     if (flow_x(f) != -32768 && flow_y(f) != -32768) {
-        const int qx = x + ((flow_x(f) + 4) >> 3), qy = y + ((flow_y(f) + 4) >> 3);
+        const int half = 4 << L, sh = 3 + L;
+        const int qx = x + ((flow_x(f) + half) >> sh), qy = y + ((flow_y(f) + half) >> sh);
         if (qx >= 0 && qx < W && qy >= 0 && qy < H) {
-            const uint32_t b = bwd[qy * W + qx];
-            if (flow_x(b) != -32768 && flow_y(b) != -32768) {
-                const long long dx = flow_x(f) + flow_x(b), dy = flow_y(f) + flow_y(b);
-                m = (dx * dx + dy * dy < (long long)eps * eps) ? 1 : 0;
+            m = 1;
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                const uint32_t b = (j == 0 ? b1 : b2)[qy * W + qx];
+                if (flow_x(b) == -32768 || flow_y(b) == -32768) {
+                    m = 0;
+                } else {
+                    const long long dx = flow_x(f) + flow_x(b), dy = flow_y(f) + flow_y(b);
+                    if (!(dx * dx + dy * dy < (long long)eps * eps)) m = 0;
+                }
             }
         }
     }
@@ -586,8 +569,10 @@ ff_status validate_config(const ff_config *c, std::string *why) {
     if (c->seed_leaf < 1 || c->seed_leaf > FF_MAX_LEAF) return *why = "seed_leaf must be 1..8", FF_EINVAL;
     if (c->seed_stride < 1 || c->seed_stride > 64) return *why = "seed_stride must be 1..64", FF_EINVAL;
     if (c->eps_q3 < 0 || c->eps_q3 > 65535) return *why = "eps_q3 out of range", FF_EINVAL;
-    if (c->schedule < FF_SCHED_BASIC || c->schedule > FF_SCHED_PLUS_FAST)
+    if (c->schedule < FF_SCHED_BASIC || c->schedule > FF_SCHED_PLUS_FAST_X2)
         return *why = "unknown schedule", FF_EINVAL;
+    if (c->schedule == FF_SCHED_PLUS_FAST_X2 && c->scales < 2)
+        return *why = "the Fast x2 schedule needs at least 2 scales", FF_EINVAL;
     if (c->max_width < 1 || c->max_width > FF_MAX_DIM || c->max_height < 1 ||
         c->max_height > FF_MAX_DIM)
         return *why = "max_width/max_height must be 1..4096", FF_EINVAL;
@@ -691,11 +676,16 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
 // 4 sweeps with 2R then 8 with R, a random search after every sweep of a
 // phase but its last; Sec. 3.4 Fast: the finest scale runs 4 sweeps with R).
 bool plus_level(const ff_config &cfg, int L) {
-    return cfg.schedule == FF_SCHED_PLUS || (cfg.schedule == FF_SCHED_PLUS_FAST && L > 0);
+    return cfg.schedule == FF_SCHED_PLUS || (cfg.schedule == FF_SCHED_PLUS_FAST && L > 0) ||
+           (cfg.schedule == FF_SCHED_PLUS_FAST_X2 && L > 1);
 }
+// Fast x2 (Sec. 3.4) never runs the finest scale: its matches are the
+// 2nd-finest scale's, one per 2x2 region
+int final_level(const ff_config &cfg) { return cfg.schedule == FF_SCHED_PLUS_FAST_X2 ? 1 : 0; }
 int level_sweeps(const ff_config &cfg, int L) {
     if (plus_level(cfg, L)) return 12;
-    if (cfg.schedule == FF_SCHED_PLUS_FAST) return 4;
+    if (L < final_level(cfg)) return 0;
+    if (cfg.schedule == FF_SCHED_PLUS_FAST || cfg.schedule == FF_SCHED_PLUS_FAST_X2) return 4;
     return cfg.iters;
 }
 bool search_after(const ff_config &cfg, int L, int t) {
@@ -796,7 +786,7 @@ ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seed
     if (s) return s;
     if (dir != FF_FWD && dir != FF_BWD && dir != FF_BWD2)
         return fail(c, FF_EINVAL, "dir must be FF_FWD, FF_BWD or FF_BWD2");
-    if (until_level < 0 || until_level >= c->S || until_sweeps < 0 ||
+    if (until_level < final_level(c->cfg) || until_level >= c->S || until_sweeps < 0 ||
         until_sweeps > level_sweeps(c->cfg, until_level))
         return fail(c, FF_EINVAL, "until_level/until_sweeps out of range");
     if (!flow_out) return fail(c, FF_EINVAL, "flow_out is NULL");
@@ -1026,7 +1016,8 @@ ff_status ff_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seeds
                    int16_t *flow_out, int32_t *cost_out) {
     if (!c) return FF_EINVAL;
     DeviceGuard guard(c->device);
-    return run_match(c, dir, pair_id, seeds_in, 0, level_sweeps(c->cfg, 0), flow_out, cost_out);
+    return run_match(c, dir, pair_id, seeds_in, final_level(c->cfg),
+                     level_sweeps(c->cfg, final_level(c->cfg)), flow_out, cost_out);
 }
 
 ff_status ff_match_until(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seeds_in,
@@ -1046,11 +1037,14 @@ ff_status ff_filter(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd,
     ff_status s = check_pair(c);
     if (s) return s;
     DeviceGuard guard(c->device);
-    const int W = c->fw[0], H = c->fh[0], N = W * H;
+    const int Lf = final_level(c->cfg);
+    int W, H;
+    level_dims(c->fw[0], c->fh[0], Lf, &W, &H);
+    const int N = W * H;
     prof_begin(c, "k_filter");
-    k_filter<<<(N + 255) / 256, 256, 0, c->stream>>>((const uint32_t *)flow_fwd,
-                                                     (const uint32_t *)flow_bwd, W, H,
-                                                     c->cfg.eps_q3, mask_out);
+    k_filter<1><<<(N + 255) / 256, 256, 0, c->stream>>>(
+        (const uint32_t *)flow_fwd, (const uint32_t *)flow_bwd, nullptr, W, H, Lf,
+        c->cfg.eps_q3, mask_out);
     return check_launch(c, "k_filter");
 }
 
@@ -1064,11 +1058,14 @@ ff_status ff_filter_2way(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow
     ff_status s = check_pair(c);
     if (s) return s;
     DeviceGuard guard(c->device);
-    const int W = c->fw[0], H = c->fh[0], N = W * H;
+    const int Lf = final_level(c->cfg);
+    int W, H;
+    level_dims(c->fw[0], c->fh[0], Lf, &W, &H);
+    const int N = W * H;
     prof_begin(c, "k_filter");
-    k_filter2<<<(N + 255) / 256, 256, 0, c->stream>>>(
-        (const uint32_t *)flow_fwd, (const uint32_t *)flow_bwd1, (const uint32_t *)flow_bwd2, W, H,
-        c->cfg.eps_q3, mask_out);
+    k_filter<2><<<(N + 255) / 256, 256, 0, c->stream>>>(
+        (const uint32_t *)flow_fwd, (const uint32_t *)flow_bwd1, (const uint32_t *)flow_bwd2, W,
+        H, Lf, c->cfg.eps_q3, mask_out);
     return check_launch(c, "k_filter");
 }
 
@@ -1080,7 +1077,11 @@ ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_
     if (w < 1 || h < 1 || w > c->maxW || h > c->maxH)
         return fail(c, FF_EINVAL, "frame size exceeds the context's max_width/max_height");
     DeviceGuard guard(c->device);
-    const size_t npix = (size_t)w * h, ibytes = npix * c->C;
+    const size_t ibytes = (size_t)w * h * c->C;
+    const int Lf = final_level(c->cfg);
+    int WL, HL;
+    level_dims(w, h, Lf, &WL, &HL);
+    const size_t npix = (size_t)WL * HL;   // points of the final grid
     cudaStream_t main = c->stream;
     ff_status s;
     if ((s = check_cuda(c, cudaMemcpyAsync(c->img_dev[0], img1_host, ibytes,
@@ -1095,11 +1096,11 @@ ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_
     if ((s = check_cuda(c, cudaEventRecord(c->ev_a, main), "event"))) return s;
     if ((s = check_cuda(c, cudaStreamWaitEvent(c->side, c->ev_a, 0), "wait"))) return s;
     c->stream = c->side;
-    s = run_match(c, FF_BWD, pair_id, nullptr, 0, level_sweeps(c->cfg, 0),
+    s = run_match(c, FF_BWD, pair_id, nullptr, Lf, level_sweeps(c->cfg, Lf),
                   (int16_t *)c->pair_flow[1], nullptr);
     c->stream = main;
     if (s) return s;
-    if ((s = run_match(c, FF_FWD, pair_id, nullptr, 0, level_sweeps(c->cfg, 0),
+    if ((s = run_match(c, FF_FWD, pair_id, nullptr, Lf, level_sweeps(c->cfg, Lf),
                        (int16_t *)c->pair_flow[0], nullptr)))
         return s;
     if ((s = check_cuda(c, cudaEventRecord(c->ev_b, c->side), "event"))) return s;

@@ -17,7 +17,7 @@ from . import _build
 
 FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_ETIMEOUT, FF_ESTATE = range(6)
 FF_FWD, FF_BWD, FF_BWD2 = 0, 1, 2
-FF_SCHED_BASIC, FF_SCHED_PLUS, FF_SCHED_PLUS_FAST = 0, 1, 2
+FF_SCHED_BASIC, FF_SCHED_PLUS, FF_SCHED_PLUS_FAST, FF_SCHED_PLUS_FAST_X2 = 0, 1, 2, 3
 FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS = 1, 2, 3
 INVALID = -32768
 
@@ -126,12 +126,19 @@ class Config:
     n_coeffs: int = 9
     schedule: int = FF_SCHED_BASIC
 
+    def final_level(self) -> int:
+        """The grid the schedule's matches come on (1 for Fast x2, else 0)."""
+        return 1 if self.schedule == FF_SCHED_PLUS_FAST_X2 else 0
+
     def sweeps(self, level: int) -> int:
         """Sweeps of `level` under this config's schedule."""
-        plus = self.schedule == FF_SCHED_PLUS or (self.schedule == FF_SCHED_PLUS_FAST and level > 0)
-        if plus:
+        s = self.schedule
+        if s == FF_SCHED_PLUS or (s == FF_SCHED_PLUS_FAST and level > 0) or \
+                (s == FF_SCHED_PLUS_FAST_X2 and level > 1):
             return 12
-        return 4 if self.schedule == FF_SCHED_PLUS_FAST else self.iters
+        if level < self.final_level():
+            return 0
+        return 4 if s in (FF_SCHED_PLUS_FAST, FF_SCHED_PLUS_FAST_X2) else self.iters
 
     def c(self) -> ff_config:
         c = ff_config()
@@ -289,17 +296,21 @@ class Context:
         ff_features(self.ctx, slot, img, W, H, W)
         self.size = (W, H)
 
-    def match(self, direction: int, pair_id: int = 0, seeds_in=None, until_level: int = 0,
-              until_sweeps: int | None = None, with_cost: bool = True):
+    def match(self, direction: int, pair_id: int = 0, seeds_in=None,
+              until_level: int | None = None, until_sweeps: int | None = None,
+              with_cost: bool = True):
         torch = self.torch
         W, H = self.size
+        Lf = self.cfg.final_level()
+        if until_level is None:
+            until_level = Lf
         if until_sweeps is None:
             until_sweeps = self.cfg.sweeps(until_level)
         WL, HL = level_dims(W, H, until_level)
         dev = torch.device("cuda", self.device)
         flow = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
         cost = torch.empty((HL, WL), dtype=torch.int32, device=dev) if with_cost else None
-        if until_level == 0 and until_sweeps == self.cfg.sweeps(0):
+        if until_level == Lf and until_sweeps == self.cfg.sweeps(Lf):
             ff_match(self.ctx, direction, pair_id, seeds_in, flow, cost)
         else:
             ff_match_until(self.ctx, direction, pair_id, seeds_in, until_level, until_sweeps,
@@ -308,15 +319,15 @@ class Context:
 
     def filter(self, flow_fwd, flow_bwd):
         torch = self.torch
-        W, H = self.size
-        mask = torch.empty((H, W), dtype=torch.uint8, device=flow_fwd.device)
+        WL, HL = level_dims(*self.size, self.cfg.final_level())
+        mask = torch.empty((HL, WL), dtype=torch.uint8, device=flow_fwd.device)
         ff_filter(self.ctx, flow_fwd, flow_bwd, mask)
         return mask
 
     def filter_2way(self, flow_fwd, flow_bwd1, flow_bwd2):
         torch = self.torch
-        W, H = self.size
-        mask = torch.empty((H, W), dtype=torch.uint8, device=flow_fwd.device)
+        WL, HL = level_dims(*self.size, self.cfg.final_level())
+        mask = torch.empty((HL, WL), dtype=torch.uint8, device=flow_fwd.device)
         ff_filter_2way(self.ctx, flow_fwd, flow_bwd1, flow_bwd2, mask)
         return mask
 
