@@ -10,6 +10,9 @@ between steps (a 256 MiB write, outside the per-step events).
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead on a
 bounded sample of the same workload.  With ``--gpus N`` (torchrun), the N
 ranks run independent replicas (the method does not shard within a pair).
+``--schedule`` selects Flow Fields+ (Sec. 3.3), Fast or Fast x2 (Sec. 3.4)
+instead of the basic schedule; ``--two-way`` adds the second backward flow
+and the two-way check of Sec. 3.7 to every step.
 """
 from __future__ import annotations
 
@@ -34,20 +37,34 @@ WORKLOAD = "sintel1024x436"
 # ----------------------------------------------------------------------------
 # helpers
 # ----------------------------------------------------------------------------
-def eval_count(W: int, H: int, S: int, I: int, leaf: int) -> int:
-    """Cost evaluations of one direction (seeding rerank + upsample re-evals +
-    2 propagation candidates + 1 random-search candidate per point and sweep,
-    fewer at the borders where a source is missing)."""
+SCHEDULES = {"basic": 0, "plus": 1, "fast": 2, "fast_x2": 3}
+
+
+def level_dims(W: int, H: int, L: int) -> tuple[int, int]:
+    s = 1 << L
+    return (W + s - 1) // s, (H + s - 1) // s
+
+
+def sweep_evals(W: int, H: int, cfg) -> int:
+    """Cost evaluations of all propagation sweeps + random searches of one
+    direction: per level and sweep 2 candidates per point (one fewer on the
+    two incoming borders), per random search 1 candidate per point."""
     n = 0
-    dims = []
-    for L in range(S):
-        s = 1 << L
-        dims.append(((W + s - 1) // s, (H + s - 1) // s))
-    n += leaf * dims[S - 1][0] * dims[S - 1][1]
-    for L, (wl, hl) in enumerate(dims):
-        n += (3 * I - 1) * wl * hl - I * (wl + hl)
-        if L < S - 1:
-            n += dims[L + 1][0] * dims[L + 1][1]
+    for L in range(cfg.scales):
+        wl, hl = level_dims(W, H, L)
+        n += cfg.sweeps(L) * (2 * wl * hl - wl - hl) + cfg.random_searches(L) * wl * hl
+    return n
+
+
+def eval_count(W: int, H: int, cfg) -> int:
+    """Cost evaluations of one direction: seeding rerank (l per coarsest
+    point), upsample re-evaluations of carried points, sweeps and searches."""
+    S = cfg.scales
+    ws, hs = level_dims(W, H, S - 1)
+    n = cfg.seed_leaf * ws * hs + sweep_evals(W, H, cfg)
+    for L in range(cfg.final_level(), S - 1):
+        wl, hl = level_dims(W, H, L + 1)
+        n += wl * hl
     return n
 
 
@@ -120,7 +137,8 @@ def measured_peaks() -> dict:
 # ----------------------------------------------------------------------------
 # CPU oracle (the baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def cpu_oracle_rate(pair, prm, budget_rows: int = 6) -> dict:
+def cpu_oracle_rate(pair, prm, schedule: int = 0, two_way: bool = False,
+                    budget_rows: int = 6) -> dict:
     """Time the oracle, as it stands, on a bounded sample of one pair.
 
     Features of both frames, the full propagation of both directions (seeded
@@ -132,7 +150,8 @@ def cpu_oracle_rate(pair, prm, budget_rows: int = 6) -> dict:
     import oracle as O
     C, S, I, R = prm["channels"], prm["scales"], prm["iters"], prm["radius_q3"]
     W, H = pair.width, pair.height
-    P = O.Params(channels=C, scales=S, iters=I, radius_q3=R)
+    stride = 2 if schedule == SCHEDULES["fast_x2"] else 1
+    P = O.Params(channels=C, scales=S, iters=I, radius_q3=R, schedule=schedule, seed_stride=stride)
     N = 1 << (S - 1)
     WS, HS = O.level_dims(W, H, S - 1)
     gt = np.rint(pair.flow * 8).astype(np.int16)
@@ -145,9 +164,10 @@ def cpu_oracle_rate(pair, prm, budget_rows: int = 6) -> dict:
     t_prop = 0.0
     rows = min(budget_rows, HS)
     flows = []
-    for d, (a, b, g) in enumerate(((f1, f2, gt), (f2, f1, -gt))):
+    dirs = [(f1, f2, gt), (f2, f1, -gt)] + ([(f2, f1, -gt)] if two_way else [])
+    for d, (a, b, g) in enumerate(dirs):
         t0 = time.perf_counter()
-        O.seed_knn_rows(a[0], b[0], S, 0, rows)
+        O.seed_knn_rows(a[0], b[0], S, 0, rows, 8, stride)
         t_seed += (time.perf_counter() - t0) * HS / rows
         seeds = np.ascontiguousarray(g[::N, ::N][:HS, :WS])
         t0 = time.perf_counter()
@@ -155,16 +175,20 @@ def cpu_oracle_rate(pair, prm, budget_rows: int = 6) -> dict:
         t_prop += time.perf_counter() - t0
         flows.append(fl)
     t0 = time.perf_counter()
-    O.filter_mask(flows[0], flows[1], 8)
+    Lf = P.final_level()
+    if two_way:
+        O.filter_mask2(flows[0], flows[1], flows[2], 8, level=Lf)
+    else:
+        O.filter_mask(flows[0], flows[1], 8, level=Lf)
     t_filt = time.perf_counter() - t0
     wall = time.perf_counter() - t_all
     per_pair = t_feat + t_seed + t_prop + t_filt
     return {"pairs_per_s": 1.0 / per_pair, "s_per_pair": per_pair, "wall_s": wall,
             "parts_s": {"features": t_feat, "seeding_scaled": t_seed, "propagation": t_prop,
                         "filter": t_filt},
-            "sample": (f"one {W}x{H} pair: features, propagation (both directions) and filter "
-                       f"in full; exact seeding on {rows} of {HS} query rows per direction, "
-                       f"scaled by {HS}/{rows}"),
+            "sample": (f"one {W}x{H} pair: features, propagation ({len(dirs)} directions) "
+                       f"and filter in full; exact seeding on {rows} of {HS} query rows per "
+                       f"direction, scaled by {HS}/{rows}"),
             "cores": 1}
 
 
@@ -181,34 +205,51 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     pair, prm = workloads.make_workload(args.workload)
     C, S, I, R = prm["channels"], prm["scales"], prm["iters"], prm["radius_q3"]
     W, H = pair.width, pair.height
-    cfg = ff.Config(channels=C, scales=S, iters=I, radius_q3=R, max_width=W, max_height=H)
+    schedule = SCHEDULES[args.schedule]
+    cfg = ff.Config(channels=C, scales=S, iters=I, radius_q3=R, max_width=W, max_height=H,
+                    schedule=schedule, seed_stride=2 if args.schedule == "fast_x2" else 1)
+    WL, HL = level_dims(W, H, cfg.final_level())
     main = torch.cuda.Stream(dev)
     side = torch.cuda.Stream(dev)
+    side2 = torch.cuda.Stream(dev)
     ctx = ff.ff_create(cfg, local_rank, main)
     if args.sweep_warps:
         ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WARPS, args.sweep_warps)
     img1 = torch.from_numpy(pair.img1).to(dev)
     img2 = torch.from_numpy(pair.img2).to(dev)
-    flow_f = torch.empty((H, W, 2), dtype=torch.int16, device=dev)
-    flow_b = torch.empty((H, W, 2), dtype=torch.int16, device=dev)
-    mask = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    flow_f = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
+    flow_b = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
+    flow_b2 = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
+    mask = torch.empty((HL, WL), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev_fork = torch.cuda.Event()
     ev_join = torch.cuda.Event()
+    ev_join2 = torch.cuda.Event()
 
-    def step(pair_id: int):
+    def step(pair_id: int, i1=img1, i2=img2):
+        # features on the main stream; the backward flow(s) on side streams
+        # overlap the forward flow; the filter joins them
         ff.ff_set_stream(ctx, main)
-        ff.ff_features(ctx, 0, img1, W, H, W)
-        ff.ff_features(ctx, 1, img2, W, H, W)
+        ff.ff_features(ctx, 0, i1, W, H, W)
+        ff.ff_features(ctx, 1, i2, W, H, W)
         ev_fork.record(main)
         side.wait_event(ev_fork)
         ff.ff_set_stream(ctx, side)
         ff.ff_match(ctx, ff.FF_BWD, pair_id, None, flow_b, None)
+        if args.two_way:
+            side2.wait_event(ev_fork)
+            ff.ff_set_stream(ctx, side2)
+            ff.ff_match(ctx, ff.FF_BWD2, pair_id, None, flow_b2, None)
         ff.ff_set_stream(ctx, main)
         ff.ff_match(ctx, ff.FF_FWD, pair_id, None, flow_f, None)
         ev_join.record(side)
         main.wait_event(ev_join)
-        ff.ff_filter(ctx, flow_f, flow_b, mask)
+        if args.two_way:
+            ev_join2.record(side2)
+            main.wait_event(ev_join2)
+            ff.ff_filter_2way(ctx, flow_f, flow_b, flow_b2, mask)
+        else:
+            ff.ff_filter(ctx, flow_f, flow_b, mask)
 
     for i in range(args.warmup):
         step(i)
@@ -243,40 +284,48 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     total_ms = sum(step_ms)
     kstats = {k: ff.ff_kernel_stats(ctx, k) for k in ff.KERNELS}
 
-    # ---- end to end through the host-buffer entry point (pinned host memory)
+    # ---- end to end from pinned host buffers: ff_pair_host (one backward
+    # flow), or the device calls above with the copies around them (two)
     h1 = torch.from_numpy(pair.img1.copy()).pin_memory()
     h2 = torch.from_numpy(pair.img2.copy()).pin_memory()
-    hf = torch.empty((H, W, 2), dtype=torch.int16).pin_memory()
-    hb = torch.empty((H, W, 2), dtype=torch.int16).pin_memory()
-    hm = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+    hf = torch.empty((HL, WL, 2), dtype=torch.int16).pin_memory()
+    hb = torch.empty((HL, WL, 2), dtype=torch.int16).pin_memory()
+    hb2 = torch.empty((HL, WL, 2), dtype=torch.int16).pin_memory()
+    hm = torch.empty((HL, WL), dtype=torch.uint8).pin_memory()
+    d1, d2 = torch.empty_like(img1), torch.empty_like(img2)
+
+    def host_step(pair_id: int):
+        if not args.two_way:
+            ff.ff_pair_host(ctx, h1, h2, W, H, pair_id, hf, hb, hm)
+            return
+        with torch.cuda.stream(main):
+            d1.copy_(h1, non_blocking=True)
+            d2.copy_(h2, non_blocking=True)
+        step(pair_id, d1, d2)
+        with torch.cuda.stream(main):
+            for dst, src in ((hf, flow_f), (hb, flow_b), (hb2, flow_b2), (hm, mask)):
+                dst.copy_(src, non_blocking=True)
+        main.synchronize()
+        ff.ff_sync(ctx)
+
     ff.ff_set_stream(ctx, main)
     for i in range(2):
-        ff.ff_pair_host(ctx, h1, h2, W, H, i, hf, hb, hm)
+        host_step(i)
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        ff.ff_pair_host(ctx, h1, h2, W, H, i, hf, hb, hm)
+        host_step(i)
     e2e_s = time.perf_counter() - t0
+    n_out = 3 if args.two_way else 2
+    e2e_bytes = (2 * C * W * H, n_out * 4 * WL * HL + WL * HL)
     ff.ff_destroy(ctx)
     return {"total_ms": total_ms, "step_ms": step_ms, "kstats": kstats, "launches": launches,
-            "clocks": clocks, "e2e_s": e2e_s, "W": W, "H": H, "C": C, "S": S, "I": I,
-            "prm": prm, "pair": pair}
+            "clocks": clocks, "e2e_s": e2e_s, "e2e_bytes": e2e_bytes, "W": W, "H": H, "C": C,
+            "S": S, "I": I, "cfg": cfg, "prm": prm, "pair": pair}
 
 
 ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock (Tops/s)
-
-
-def sweep_evals(W: int, H: int, S: int, I: int) -> int:
-    """Cost evaluations of all propagation sweeps + random searches of one
-    direction: per level, I sweeps of 2 candidates per point (one fewer on
-    the two incoming borders) and I-1 random searches of 1 candidate."""
-    n = 0
-    for L in range(S):
-        s = 1 << L
-        wl, hl = (W + s - 1) // s, (H + s - 1) // s
-        n += I * (2 * wl * hl - wl - hl) + (I - 1) * wl * hl
-    return n
 
 
 def recorded_traffic(kernel: str) -> float | None:
@@ -294,7 +343,7 @@ def recorded_traffic(kernel: str) -> float | None:
         return None
 
 
-def roofline(res: dict, steps: int) -> dict:
+def roofline(res: dict, steps: int, n_dirs: int) -> dict:
     """Roofline of the kernel with the largest share of device time.
 
     k_sweep (propagation + random search) is integer-ALU work on a serial
@@ -315,7 +364,8 @@ def roofline(res: dict, steps: int) -> dict:
     share = ms / sum(tot.values())
     avg_ms = ms / max(n_launch, 1)
     if dom == "k_sweep":
-        ops_per_launch = 2 * steps * sweep_evals(W, H, S, I) * 9 * C * 10 / max(n_launch, 1)
+        ops_per_launch = n_dirs * steps * sweep_evals(W, H, res["cfg"]) * 9 * C * 10 / \
+            max(n_launch, 1)
         achieved = ops_per_launch / (avg_ms / 1e3) / 1e12
         return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
                 "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
@@ -325,7 +375,8 @@ def roofline(res: dict, steps: int) -> dict:
         N = 1 << (S - 1)
         nq = ((W + N - 1) // N) * ((H + N - 1) // N)
         K = 16 if C == 1 else 32
-        flops = 2 * steps * 2 * nq * W * H * K * 2 * (1 + 1 / 16) / max(n_launch, 1)
+        ncand = ((W + 1) // 2) * ((H + 1) // 2) if res["cfg"].seed_stride == 2 else W * H
+        flops = n_dirs * steps * 2 * nq * ncand * K * 2 * (1 + 1 / 16) / max(n_launch, 1)
         peak = measured_peaks().get("bf16_tflops", 1900.0)
         achieved = flops / (avg_ms / 1e3) / 1e12
         return {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
@@ -345,6 +396,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", choices=sorted(SCHEDULES), default="basic",
+                    help="sweep schedule: basic (Sec. 3.1-3.2), plus (Flow Fields+), fast, "
+                         "fast_x2 (Sec. 3.3-3.4)")
+    ap.add_argument("--two-way", action="store_true",
+                    help="second backward flow and two-way check (Sec. 3.7)")
     ap.add_argument("--sweep-warps", type=int, default=0,
                     help="propagation warps per sweep CTA (1, 2, 4; 0 = library default)")
     args = ap.parse_args()
@@ -363,7 +419,8 @@ def main():
         rates = []
         sample = None
         for _ in range(max(1, args.steps)):
-            r = cpu_oracle_rate(pair, prm, budget_rows=2)
+            r = cpu_oracle_rate(pair, prm, SCHEDULES[args.schedule], args.two_way,
+                                budget_rows=2)
             rates.append(r["pairs_per_s"])
             sample = r["sample"]
         v = statistics.median(rates)
@@ -373,7 +430,9 @@ def main():
                 "vs_baseline": None, "dtype": "int8", "data": "synthetic",
                 "config": {"workload": args.workload, "frame": f"{pair.width}x{pair.height}",
                            "channels": prm["channels"], "scales": prm["scales"],
-                           "iters": prm["iters"], "radius_q3": prm["radius_q3"]},
+                           "iters": prm["iters"], "radius_q3": prm["radius_q3"],
+                           "schedule": args.schedule,
+                           "backward_flows": 2 if args.two_way else 1},
                 "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
@@ -402,7 +461,8 @@ def main():
     pairs = K * world
     value = pairs / total_s
     W, H, C, S, I = res["W"], res["H"], res["C"], res["S"], res["I"]
-    evals_pair = 2 * eval_count(W, H, S, I, 8)
+    n_dirs = 3 if args.two_way else 2
+    evals_pair = n_dirs * eval_count(W, H, res["cfg"])
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": res["total_ms"] / K, "higher_is_better": True,
@@ -410,21 +470,23 @@ def main():
         "evals_per_s": evals_pair * pairs / total_s,
         "config": {"workload": args.workload, "frame": f"{W}x{H}", "channels": C, "scales": S,
                    "iters": I, "radius_q3": res["prm"]["radius_q3"], "seed_leaf": 8,
+                   "schedule": args.schedule, "seed_stride": res["cfg"].seed_stride,
+                   "backward_flows": n_dirs - 1,
                    "l2": "flushed between steps (256 MiB write outside the step events)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
         "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
-                "h2d_bytes_per_step": 2 * C * W * H,
-                "d2h_bytes_per_step": 2 * 4 * W * H + W * H},
-        "roofline": roofline(res, K),
+                "h2d_bytes_per_step": res["e2e_bytes"][0],
+                "d2h_bytes_per_step": res["e2e_bytes"][1]},
+        "roofline": roofline(res, K, n_dirs),
         "kernels_ms": {k: round(v[1], 4) for k, v in res["kstats"].items() if v[0]},
     }
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
     if not args.no_cpu_baseline and world == 1:
-        r = cpu_oracle_rate(res["pair"], res["prm"])
+        r = cpu_oracle_rate(res["pair"], res["prm"], SCHEDULES[args.schedule], args.two_way)
         line["cpu_baseline"] = {"value": r["pairs_per_s"], "unit": "pairs/s",
                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
                                 "wall_s": round(r["wall_s"], 2)}

@@ -140,6 +140,12 @@ class Config:
             return 0
         return 4 if s in (FF_SCHED_PLUS_FAST, FF_SCHED_PLUS_FAST_X2) else self.iters
 
+    def random_searches(self, level: int) -> int:
+        """Random-search passes of `level`: one after every sweep of a phase
+        but its last (two phases on Flow Fields+ levels)."""
+        n = self.sweeps(level)
+        return n - 2 if n == 12 and self.schedule != FF_SCHED_BASIC else max(n - 1, 0)
+
     def c(self) -> ff_config:
         c = ff_config()
         lib().ff_config_default(ct.byref(c))
