@@ -233,6 +233,60 @@ const char *ff_last_error(const ff_ctx *ctx);
 const char *ff_status_string(ff_status s);
 void ff_destroy(ff_ctx *ctx);
 
+/* ---- Batched form --------------------------------------------------------
+ * Many frame pairs of mixed sizes in flight at once.  The paper matches one
+ * pair at a time (Sec. 3); this form has no counterpart there.  It changes
+ * nothing in what a pair computes: every pair's flows and mask equal those of
+ * ff_features + ff_match + ff_filter (or ff_filter_2way) on one context with
+ * the same config and pair_id.
+ *
+ * A batch owns `slots` matching slots; each holds its own features, states
+ * and streams for frames up to cfg.max_width x cfg.max_height.  ff_batch_run
+ * deals pairs round-robin to the slots: pairs in different slots overlap on
+ * the device, so their sweeps' wavefronts share the SMs; pairs in one slot
+ * run in order. */
+typedef struct ff_batch ff_batch;
+
+typedef struct {
+    const uint8_t *img1;  /* device, planar uint8 [channels][h][pitch]; read only     */
+    const uint8_t *img2;
+    int w, h, pitch;      /* 1 <= w <= max_width, 1 <= h <= max_height, pitch >= w     */
+    uint32_t pair_id;     /* random-search key word 1                                  */
+    int16_t *flow_fwd;    /* device, final grid [..][..][2] (see ff_schedule); required */
+    int16_t *flow_bwd;    /* device, final grid; required                              */
+    int16_t *flow_bwd2;   /* device, final grid, or NULL: one backward flow            */
+    uint8_t *mask;        /* device, final grid, or NULL: no filter                    */
+} ff_pair_desc;
+
+/* Creates a batch of `slots` (1..256) slots on `device`; the work of each
+ * ff_batch_run joins back into cuda_stream (NULL = legacy default stream).
+ * Allocates all device memory up front: per slot, what ff_create allocates,
+ * plus one stream. */
+ff_status ff_batch_create(const ff_config *cfg, int device, int slots, void *cuda_stream,
+                          ff_batch **out);
+
+/* Enqueues n pairs (n >= 0) and returns without waiting; the batch's stream
+ * is ordered after all of them.  The caller owns every buffer and keeps it
+ * alive until that point; output buffers of different pairs must not
+ * overlap.  Descriptors are checked before anything is enqueued (FF_EINVAL,
+ * nothing launched).  use_graph != 0: the whole enqueue is captured as one
+ * CUDA graph and launched; a later call with the same n and identical
+ * descriptors relaunches that graph without capturing again. */
+ff_status ff_batch_run(ff_batch *b, int n, const ff_pair_desc *pairs, int use_graph);
+
+/* Makes later ff_batch_run calls join into another stream. */
+ff_status ff_batch_set_stream(ff_batch *b, void *cuda_stream);
+
+/* Waits for the device and reports FF_ETIMEOUT if a bounded wait of any
+ * slot expired (the words are cleared). */
+ff_status ff_batch_sync(ff_batch *b);
+
+/* Kernel launches made by this batch so far (graph relaunches included). */
+long long ff_batch_launch_count(const ff_batch *b);
+
+const char *ff_batch_last_error(const ff_batch *b);
+void ff_batch_destroy(ff_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

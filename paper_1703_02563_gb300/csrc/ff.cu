@@ -394,7 +394,6 @@ struct DirState {
     float *t0 = nullptr;                      //   upper bounds of their 8th key
     __nv_bfloat16 *cbf = nullptr;             // seeding candidates, bf16 rows of K
     int *err = nullptr;
-    uint32_t epoch = 0;
 };
 
 }  // namespace
@@ -403,8 +402,8 @@ struct ff_ctx {
     ff_config cfg;
     int device = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr;   // backward flows 1 and 2
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
     int C = 1, P = 16, S = 4, I = 4;
     int maxW = 0, maxH = 0;
     size_t feat_cap = 0;
@@ -555,8 +554,10 @@ void free_all(ff_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->side2) cudaStreamDestroy(c->side2);
     if (c->ev_a) cudaEventDestroy(c->ev_a);
     if (c->ev_b) cudaEventDestroy(c->ev_b);
+    if (c->ev_c) cudaEventDestroy(c->ev_c);
 }
 
 ff_status validate_config(const ff_config *c, std::string *why) {
@@ -722,8 +723,10 @@ ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L,
     a.radius_q3 = search_radius(c->cfg, L, t);
     a.seed = c->cfg.seed;
     a.pair_id = pair_id;
-    a.epoch = ++st.epoch;
-    if (st.epoch == 0x7fffffffu) st.epoch = 0;   // epochs stay below bit 31
+    // boundary-row tags: unique per (level, sweep) within a match (the rows
+    // are cleared when a match starts), never 0, below bit 31; the same in
+    // every replay of a captured graph
+    a.epoch = 1u + (uint32_t)(L * kMaxIters + t);
     a.wait_ns = c->wait_ns;
     a.force_timeout = c->force_timeout;
     const int R = rows_per_strip(c->C, c->sweep_warps);
@@ -801,6 +804,10 @@ ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seed
                                       c->stream),
                    "memset tickets");
     if (s) return s;
+    s = check_cuda(c, cudaMemsetAsync(st.edge, 0, c->edge_cap * sizeof(unsigned long long),
+                                      c->stream),
+                   "clear boundary rows");
+    if (s) return s;
     int cur = 0, WP = 0;
     for (int L = c->S - 1; L >= until_level; L--) {
         int WL, HL;
@@ -850,6 +857,80 @@ ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seed
     k_export<<<(N + 255) / 256, 256, 0, c->stream>>>(st.flow[cur], st.cost[cur], N,
                                                      (uint32_t *)flow_out, (int *)cost_out);
     return check_launch(c, "k_export");
+}
+
+ff_status filter_into(ff_ctx *c, const int16_t *fwd, const int16_t *b1, const int16_t *b2,
+                      uint8_t *mask);
+
+// One whole pair on device buffers, enqueued without waiting: features on
+// the context's stream, the backward flow(s) on the side stream(s)
+// overlapping the forward flow, the filter after all of them.  The next
+// work on the context's stream is ordered after every part.
+ff_status enqueue_pair(ff_ctx *c, const uint8_t *img1, const uint8_t *img2, int w, int h,
+                       int pitch, uint32_t pair_id, int16_t *fwd, int16_t *bwd, int16_t *bwd2,
+                       uint8_t *mask) {
+    const int Lf = final_level(c->cfg);
+    const int n = level_sweeps(c->cfg, Lf);
+    cudaStream_t main = c->stream;
+    ff_status s;
+    if ((s = ff_features(c, 0, img1, w, h, pitch))) return s;
+    if ((s = ff_features(c, 1, img2, w, h, pitch))) return s;
+    if ((s = check_cuda(c, cudaEventRecord(c->ev_a, main), "event"))) return s;
+    if ((s = check_cuda(c, cudaStreamWaitEvent(c->side, c->ev_a, 0), "wait"))) return s;
+    c->stream = c->side;
+    s = run_match(c, FF_BWD, pair_id, nullptr, Lf, n, bwd, nullptr);
+    c->stream = main;
+    if (s) return s;
+    if (bwd2) {
+        if ((s = check_cuda(c, cudaStreamWaitEvent(c->side2, c->ev_a, 0), "wait"))) return s;
+        c->stream = c->side2;
+        s = run_match(c, FF_BWD2, pair_id, nullptr, Lf, n, bwd2, nullptr);
+        c->stream = main;
+        if (s) return s;
+    }
+    if ((s = run_match(c, FF_FWD, pair_id, nullptr, Lf, n, fwd, nullptr))) return s;
+    if ((s = check_cuda(c, cudaEventRecord(c->ev_b, c->side), "event"))) return s;
+    if ((s = check_cuda(c, cudaStreamWaitEvent(main, c->ev_b, 0), "wait"))) return s;
+    if (bwd2) {
+        if ((s = check_cuda(c, cudaEventRecord(c->ev_c, c->side2), "event"))) return s;
+        if ((s = check_cuda(c, cudaStreamWaitEvent(main, c->ev_c, 0), "wait"))) return s;
+    }
+    if (mask) return filter_into(c, fwd, bwd, bwd2, mask);
+    return FF_OK;
+}
+
+// reads and clears the context's device error words (after a synchronize)
+ff_status take_error_words(ff_ctx *c) {
+    int err[kNumDirs] = {0, 0, 0};
+    ff_status s;
+    for (int d = 0; d < kNumDirs; d++)
+        if ((s = check_cuda(c, cudaMemcpy(&err[d], c->dir[d].err, sizeof(int),
+                                          cudaMemcpyDeviceToHost), "read error word")))
+            return s;
+    if (err[0] || err[1] || err[2]) {
+        for (int d = 0; d < kNumDirs; d++) cudaMemset(c->dir[d].err, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        return fail(c, FF_ETIMEOUT, "a bounded device wait expired during matching");
+    }
+    return FF_OK;
+}
+
+// Sec. 3.7 on the schedule's final grid, against one or two backward flows
+ff_status filter_into(ff_ctx *c, const int16_t *fwd, const int16_t *b1, const int16_t *b2,
+                      uint8_t *mask) {
+    const int Lf = final_level(c->cfg);
+    int W, H;
+    level_dims(c->fw[0], c->fh[0], Lf, &W, &H);
+    const int N = W * H;
+    prof_begin(c, "k_filter");
+    if (b2)
+        k_filter<2><<<(N + 255) / 256, 256, 0, c->stream>>>(
+            (const uint32_t *)fwd, (const uint32_t *)b1, (const uint32_t *)b2, W, H, Lf,
+            c->cfg.eps_q3, mask);
+    else
+        k_filter<1><<<(N + 255) / 256, 256, 0, c->stream>>>(
+            (const uint32_t *)fwd, (const uint32_t *)b1, nullptr, W, H, Lf, c->cfg.eps_q3, mask);
+    return check_launch(c, "k_filter");
 }
 
 }  // namespace
@@ -964,8 +1045,10 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     }
     if (e == cudaSuccess) e = alloc(&c->pair_mask, npix);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_c, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         const ff_status s = (e == cudaErrorMemoryAllocation) ? FF_ENOMEM : FF_ECUDA;
@@ -1037,15 +1120,7 @@ ff_status ff_filter(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd,
     ff_status s = check_pair(c);
     if (s) return s;
     DeviceGuard guard(c->device);
-    const int Lf = final_level(c->cfg);
-    int W, H;
-    level_dims(c->fw[0], c->fh[0], Lf, &W, &H);
-    const int N = W * H;
-    prof_begin(c, "k_filter");
-    k_filter<1><<<(N + 255) / 256, 256, 0, c->stream>>>(
-        (const uint32_t *)flow_fwd, (const uint32_t *)flow_bwd, nullptr, W, H, Lf,
-        c->cfg.eps_q3, mask_out);
-    return check_launch(c, "k_filter");
+    return filter_into(c, flow_fwd, flow_bwd, nullptr, mask_out);
 }
 
 ff_status ff_filter_2way(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd1,
@@ -1058,15 +1133,7 @@ ff_status ff_filter_2way(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow
     ff_status s = check_pair(c);
     if (s) return s;
     DeviceGuard guard(c->device);
-    const int Lf = final_level(c->cfg);
-    int W, H;
-    level_dims(c->fw[0], c->fh[0], Lf, &W, &H);
-    const int N = W * H;
-    prof_begin(c, "k_filter");
-    k_filter<2><<<(N + 255) / 256, 256, 0, c->stream>>>(
-        (const uint32_t *)flow_fwd, (const uint32_t *)flow_bwd1, (const uint32_t *)flow_bwd2, W,
-        H, Lf, c->cfg.eps_q3, mask_out);
-    return check_launch(c, "k_filter");
+    return filter_into(c, flow_fwd, flow_bwd1, flow_bwd2, mask_out);
 }
 
 ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_host, int w,
@@ -1090,23 +1157,9 @@ ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_
     if ((s = check_cuda(c, cudaMemcpyAsync(c->img_dev[1], img2_host, ibytes,
                                            cudaMemcpyHostToDevice, main), "copy img2")))
         return s;
-    if ((s = ff_features(c, 0, c->img_dev[0], w, h, w))) return s;
-    if ((s = ff_features(c, 1, c->img_dev[1], w, h, w))) return s;
-    // backward matching on the side stream, forward on the caller's stream
-    if ((s = check_cuda(c, cudaEventRecord(c->ev_a, main), "event"))) return s;
-    if ((s = check_cuda(c, cudaStreamWaitEvent(c->side, c->ev_a, 0), "wait"))) return s;
-    c->stream = c->side;
-    s = run_match(c, FF_BWD, pair_id, nullptr, Lf, level_sweeps(c->cfg, Lf),
-                  (int16_t *)c->pair_flow[1], nullptr);
-    c->stream = main;
-    if (s) return s;
-    if ((s = run_match(c, FF_FWD, pair_id, nullptr, Lf, level_sweeps(c->cfg, Lf),
-                       (int16_t *)c->pair_flow[0], nullptr)))
-        return s;
-    if ((s = check_cuda(c, cudaEventRecord(c->ev_b, c->side), "event"))) return s;
-    if ((s = check_cuda(c, cudaStreamWaitEvent(main, c->ev_b, 0), "wait"))) return s;
-    if ((s = ff_filter(c, (const int16_t *)c->pair_flow[0], (const int16_t *)c->pair_flow[1],
-                       c->pair_mask)))
+    if ((s = enqueue_pair(c, c->img_dev[0], c->img_dev[1], w, h, w, pair_id,
+                          (int16_t *)c->pair_flow[0], (int16_t *)c->pair_flow[1], nullptr,
+                          c->pair_mask)))
         return s;
     if (flow_fwd_host &&
         (s = check_cuda(c, cudaMemcpyAsync(flow_fwd_host, c->pair_flow[0], npix * 4,
@@ -1121,16 +1174,7 @@ ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_
                                            main), "copy mask")))
         return s;
     if ((s = check_cuda(c, cudaStreamSynchronize(main), "synchronize"))) return s;
-    int err[kNumDirs] = {0, 0, 0};
-    for (int d = 0; d < kNumDirs; d++)
-        if ((s = check_cuda(c, cudaMemcpy(&err[d], c->dir[d].err, sizeof(int),
-                                          cudaMemcpyDeviceToHost), "read error word")))
-            return s;
-    if (err[0] || err[1] || err[2]) {
-        for (int d = 0; d < kNumDirs; d++) cudaMemset(c->dir[d].err, 0, sizeof(int));
-        return fail(c, FF_ETIMEOUT, "a bounded device wait expired during matching");
-    }
-    return FF_OK;
+    return take_error_words(c);
 }
 
 ff_status ff_get_features(ff_ctx *c, int slot, int level, int8_t *dst) {
@@ -1234,18 +1278,7 @@ ff_status ff_sync(ff_ctx *c) {
     DeviceGuard guard(c->device);
     ff_status s = check_cuda(c, cudaDeviceSynchronize(), "synchronize");
     if (s) return s;
-    int err[kNumDirs] = {0, 0, 0};
-    for (int d = 0; d < kNumDirs; d++) {
-        s = check_cuda(c, cudaMemcpy(&err[d], c->dir[d].err, sizeof(int), cudaMemcpyDeviceToHost),
-                       "read error word");
-        if (s) return s;
-    }
-    if (err[0] || err[1] || err[2]) {
-        for (int d = 0; d < kNumDirs; d++) cudaMemset(c->dir[d].err, 0, sizeof(int));
-        cudaDeviceSynchronize();
-        return fail(c, FF_ETIMEOUT, "a bounded device wait expired during matching");
-    }
-    return FF_OK;
+    return take_error_words(c);
 }
 
 ff_status ff_debug_set(ff_ctx *c, ff_debug_key key, long long value) {
@@ -1323,6 +1356,232 @@ void ff_destroy(ff_ctx *c) {
         free_all(c);
     }
     delete c;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// batched form
+// ============================================================================
+struct ff_batch {
+    ff_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;              // the caller's stream
+    std::vector<ff_ctx *> slot;
+    std::vector<cudaStream_t> slot_stream;      // one per slot, owned
+    std::vector<cudaEvent_t> ev_join;           // one per slot
+    cudaEvent_t ev_fork = nullptr;
+    cudaStream_t capture = nullptr;             // graphs are captured here, owned
+    // the last captured graph and the descriptors it was captured for
+    cudaGraphExec_t exec = nullptr;
+    std::vector<ff_pair_desc> exec_desc;
+    long long exec_launches = 0;
+    long long launches = 0;
+    std::string last_error;
+};
+
+namespace {
+
+ff_status bfail(ff_batch *b, ff_status s, const std::string &msg) {
+    b->last_error = msg;
+    return s;
+}
+
+void batch_free(ff_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (ff_ctx *c : b->slot) ff_destroy(c);
+    for (cudaStream_t s : b->slot_stream)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev_join)
+        if (e) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->capture) cudaStreamDestroy(b->capture);
+}
+
+long long slot_launches(const ff_batch *b) {
+    long long n = 0;
+    for (const ff_ctx *c : b->slot) n += c->launches;
+    return n;
+}
+
+bool same_desc(const ff_pair_desc &x, const ff_pair_desc &y) {
+    return x.img1 == y.img1 && x.img2 == y.img2 && x.w == y.w && x.h == y.h &&
+           x.pitch == y.pitch && x.pair_id == y.pair_id && x.flow_fwd == y.flow_fwd &&
+           x.flow_bwd == y.flow_bwd && x.flow_bwd2 == y.flow_bwd2 && x.mask == y.mask;
+}
+
+// fork from `origin` to the used slots, enqueue every pair on its slot,
+// join back into `origin`
+ff_status batch_enqueue(ff_batch *b, cudaStream_t origin, int n, const ff_pair_desc *pairs) {
+    const int used = n < (int)b->slot.size() ? n : (int)b->slot.size();
+    ff_status s;
+    if (used == 0) return FF_OK;
+    if ((s = check_cuda(b->slot[0], cudaEventRecord(b->ev_fork, origin), "event")))
+        return bfail(b, s, b->slot[0]->last_error);
+    for (int j = 0; j < used; j++)
+        if ((s = check_cuda(b->slot[j], cudaStreamWaitEvent(b->slot_stream[j], b->ev_fork, 0),
+                            "wait")))
+            return bfail(b, s, b->slot[j]->last_error);
+    for (int i = 0; i < n; i++) {
+        const ff_pair_desc &p = pairs[i];
+        ff_ctx *c = b->slot[i % used];
+        if ((s = enqueue_pair(c, p.img1, p.img2, p.w, p.h, p.pitch, p.pair_id, p.flow_fwd,
+                              p.flow_bwd, p.flow_bwd2, p.mask)))
+            return bfail(b, s, "pair " + std::to_string(i) + ": " + c->last_error);
+    }
+    for (int j = 0; j < used; j++) {
+        if ((s = check_cuda(b->slot[j], cudaEventRecord(b->ev_join[j], b->slot_stream[j]),
+                            "event")))
+            return bfail(b, s, b->slot[j]->last_error);
+        if ((s = check_cuda(b->slot[j], cudaStreamWaitEvent(origin, b->ev_join[j], 0),
+                            "wait")))
+            return bfail(b, s, b->slot[j]->last_error);
+    }
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ff_status ff_batch_create(const ff_config *cfg, int device, int slots, void *cuda_stream,
+                          ff_batch **out) {
+    if (!cfg || !out) return FF_EINVAL;
+    *out = nullptr;
+    if (slots < 1 || slots > 256) return FF_EINVAL;
+    std::string why;
+    if (validate_config(cfg, &why) != FF_OK) return FF_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FF_ECUDA;
+    DeviceGuard guard(device);
+    ff_batch *b = new ff_batch();
+    b->cfg = *cfg;
+    b->device = device;
+    b->stream = (cudaStream_t)cuda_stream;
+    ff_status s = FF_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    for (int i = 0; i < slots && e == cudaSuccess && s == FF_OK; i++) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        b->slot_stream.push_back(st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        b->ev_join.push_back(ev);
+        if (e != cudaSuccess) break;
+        ff_ctx *c = nullptr;
+        s = ff_create(cfg, device, st, &c);
+        if (s == FF_OK) b->slot.push_back(c);
+    }
+    if (e != cudaSuccess || s != FF_OK) {
+        batch_free(b);
+        delete b;
+        cudaGetLastError();
+        return s != FF_OK ? s : (e == cudaErrorMemoryAllocation ? FF_ENOMEM : FF_ECUDA);
+    }
+    *out = b;
+    return FF_OK;
+}
+
+ff_status ff_batch_run(ff_batch *b, int n, const ff_pair_desc *pairs, int use_graph) {
+    if (!b) return FF_EINVAL;
+    if (n < 0 || (n > 0 && !pairs)) return bfail(b, FF_EINVAL, "bad pair count or array");
+    for (int i = 0; i < n; i++) {
+        const ff_pair_desc &p = pairs[i];
+        const std::string at = "pair " + std::to_string(i) + ": ";
+        if (!p.img1 || !p.img2 || !p.flow_fwd || !p.flow_bwd)
+            return bfail(b, FF_EINVAL, at + "NULL image or flow");
+        if (p.w < 1 || p.h < 1 || p.w > b->cfg.max_width || p.h > b->cfg.max_height)
+            return bfail(b, FF_EINVAL, at + "frame size exceeds max_width/max_height");
+        if (p.pitch < p.w) return bfail(b, FF_EINVAL, at + "pitch < width");
+        if (((uintptr_t)p.flow_fwd & 3) || ((uintptr_t)p.flow_bwd & 3) ||
+            ((uintptr_t)p.flow_bwd2 & 3))
+            return bfail(b, FF_EINVAL, at + "flows must be 4-byte aligned");
+    }
+    DeviceGuard guard(b->device);
+    if (use_graph && b->exec && (int)b->exec_desc.size() == n) {
+        bool same = true;
+        for (int i = 0; i < n && same; i++) same = same_desc(b->exec_desc[i], pairs[i]);
+        if (same) {
+            const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+            if (e != cudaSuccess)
+                return bfail(b, FF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+            b->launches += b->exec_launches;
+            return FF_OK;
+        }
+    }
+    const long long l0 = slot_launches(b);
+    if (!use_graph) {
+        const ff_status s = batch_enqueue(b, b->stream, n, pairs);
+        b->launches += slot_launches(b) - l0;
+        return s;
+    }
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        b->exec_desc.clear();
+    }
+    // captured on the batch's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured), launched into the caller's
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return bfail(b, FF_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    const ff_status s = batch_enqueue(b, b->capture, n, pairs);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->capture, &graph);
+    if (s != FF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return s;
+    }
+    if (e != cudaSuccess)
+        return bfail(b, FF_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return bfail(b, FF_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    b->exec_desc.assign(pairs, pairs + n);
+    b->exec_launches = slot_launches(b) - l0;
+    e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess)
+        return bfail(b, FF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    b->launches += b->exec_launches;
+    return FF_OK;
+}
+
+ff_status ff_batch_set_stream(ff_batch *b, void *cuda_stream) {
+    if (!b) return FF_EINVAL;
+    b->stream = (cudaStream_t)cuda_stream;
+    return FF_OK;
+}
+
+ff_status ff_batch_sync(ff_batch *b) {
+    if (!b) return FF_EINVAL;
+    DeviceGuard guard(b->device);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+        return bfail(b, FF_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+    for (ff_ctx *c : b->slot) {
+        const ff_status s = take_error_words(c);
+        if (s) return bfail(b, s, c->last_error);
+    }
+    return FF_OK;
+}
+
+long long ff_batch_launch_count(const ff_batch *b) { return b ? b->launches : 0; }
+
+const char *ff_batch_last_error(const ff_batch *b) { return b ? b->last_error.c_str() : ""; }
+
+void ff_batch_destroy(ff_batch *b) {
+    if (!b) return;
+    {
+        DeviceGuard guard(b->device);
+        cudaDeviceSynchronize();
+        batch_free(b);
+    }
+    delete b;
 }
 
 }  // extern "C"

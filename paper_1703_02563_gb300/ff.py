@@ -24,7 +24,9 @@ INVALID = -32768
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
             "ff_match_until", "ff_filter", "ff_filter_2way", "ff_pair_host", "ff_get_features", "ff_seed_knn",
             "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
-            "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy")
+            "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy",
+            "ff_batch_create", "ff_batch_run", "ff_batch_set_stream", "ff_batch_sync",
+            "ff_batch_launch_count", "ff_batch_last_error", "ff_batch_destroy")
 
 
 class ff_config(ct.Structure):
@@ -33,6 +35,12 @@ class ff_config(ct.Structure):
                 ("seed_leaf", ct.c_int), ("seed_stride", ct.c_int), ("eps_q3", ct.c_int),
                 ("seed", ct.c_uint32), ("max_width", ct.c_int), ("max_height", ct.c_int),
                 ("schedule", ct.c_int)]
+
+
+class ff_pair_desc(ct.Structure):
+    _fields_ = [("img1", ct.c_void_p), ("img2", ct.c_void_p), ("w", ct.c_int), ("h", ct.c_int),
+                ("pitch", ct.c_int), ("pair_id", ct.c_uint32), ("flow_fwd", ct.c_void_p),
+                ("flow_bwd", ct.c_void_p), ("flow_bwd2", ct.c_void_p), ("mask", ct.c_void_p)]
 
 
 class FFError(RuntimeError):
@@ -77,9 +85,20 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_status_string.restype = ct.c_char_p
         L.ff_destroy.argtypes = [P]
         L.ff_destroy.restype = None
+        L.ff_batch_create.argtypes = [ct.POINTER(ff_config), i, i, P, ct.POINTER(P)]
+        L.ff_batch_run.argtypes = [P, i, ct.POINTER(ff_pair_desc), i]
+        L.ff_batch_set_stream.argtypes = [P, P]
+        L.ff_batch_sync.argtypes = [P]
+        L.ff_batch_launch_count.argtypes = [P]
+        L.ff_batch_launch_count.restype = ct.c_longlong
+        L.ff_batch_last_error.argtypes = [P]
+        L.ff_batch_last_error.restype = ct.c_char_p
+        L.ff_batch_destroy.argtypes = [P]
+        L.ff_batch_destroy.restype = None
         for name in EXPORTED:
             if name not in ("ff_last_error", "ff_status_string", "ff_destroy",
-                            "ff_launch_count"):
+                            "ff_launch_count", "ff_batch_launch_count", "ff_batch_last_error",
+                            "ff_batch_destroy"):
                 getattr(L, name).restype = ct.c_int
         _lib = L
     return _lib
@@ -358,3 +377,52 @@ class Context:
 
     def sync(self):
         ff_sync(self.ctx)
+
+
+# ---- batched form ----------------------------------------------------------
+def _bcheck(b, status: int):
+    if status != FF_OK:
+        msg = lib().ff_batch_last_error(b).decode() if b else ""
+        raise FFError(status, msg)
+
+
+def ff_batch_create(cfg: Config, device: int = 0, slots: int = 8, stream=None) -> int:
+    out = ct.c_void_p()
+    c = cfg.c()
+    _bcheck(None, lib().ff_batch_create(ct.byref(c), device, slots, _stream_handle(stream),
+                                        ct.byref(out)))
+    return out.value
+
+
+def pair_descs(pairs) -> ct.Array:
+    """ff_pair_desc array from dicts with keys img1, img2, w, h, pitch (default
+    w), pair_id, flow_fwd, flow_bwd, flow_bwd2 (optional), mask (optional)."""
+    arr = (ff_pair_desc * max(len(pairs), 1))()
+    for k, p in enumerate(pairs):
+        arr[k] = ff_pair_desc(_ptr(p["img1"]), _ptr(p["img2"]), p["w"], p["h"],
+                              p.get("pitch", p["w"]), p.get("pair_id", 0), _ptr(p["flow_fwd"]),
+                              _ptr(p["flow_bwd"]), _ptr(p.get("flow_bwd2")), _ptr(p.get("mask")))
+    return arr
+
+
+def ff_batch_run(b: int, descs, n: int | None = None, use_graph: bool = False) -> None:
+    if not isinstance(descs, ct.Array):
+        n = len(descs)
+        descs = pair_descs(descs)
+    _bcheck(b, lib().ff_batch_run(b, len(descs) if n is None else n, descs, int(use_graph)))
+
+
+def ff_batch_set_stream(b: int, stream) -> None:
+    _bcheck(b, lib().ff_batch_set_stream(b, _stream_handle(stream)))
+
+
+def ff_batch_sync(b: int) -> None:
+    _bcheck(b, lib().ff_batch_sync(b))
+
+
+def ff_batch_launch_count(b: int) -> int:
+    return int(lib().ff_batch_launch_count(b))
+
+
+def ff_batch_destroy(b: int) -> None:
+    lib().ff_batch_destroy(b)

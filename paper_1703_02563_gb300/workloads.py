@@ -482,3 +482,54 @@ def make_workload(name: str) -> tuple[FramePair, dict]:
     params = dict(scales=spec["scales"], iters=spec["iters"], radius_q3=spec["radius_q3"],
                   channels=pair.channels)
     return pair, params
+
+
+# ----------------------------------------------------------------------------
+# batched workload: many pairs of mixed sizes in one Lab configuration
+# ----------------------------------------------------------------------------
+BATCH_SIZES = ((320, 240), (640, 480), (1024, 436), (1242, 375))
+# matching parameters of the batch (those of the Sintel-shaped pair)
+BATCH_PARAMS = dict(channels=3, scales=4, iters=6, radius_q3=8)
+
+
+def _gray_to_lab(pair: FramePair) -> FramePair:
+    """A gray pair as 8-bit CIELab frames (r = g = b = gray): L carries the
+    image, a and b sit at their neutral 128."""
+    to_lab = lambda g: rgb_to_lab_u8(np.repeat(g.astype(np.float64) / 255.0, 3, axis=0))
+    return FramePair(to_lab(pair.img1), to_lab(pair.img2), pair.flow, pair.occ,
+                     pair.name + "-lab")
+
+
+def batch_pair(seed: int, k: int, sizes=BATCH_SIZES) -> FramePair:
+    """Pair k of the mixed batch: a size drawn uniformly from `sizes` and,
+    alternately, the layered Sintel-shaped generator (displacement scaled to
+    the frame: 150 px at 1024 wide) or the translation generator of the tiny
+    workload (a per-pair global shift up to 3 % of the width, promoted to Lab)."""
+    rng = np.random.default_rng([seed, k])
+    w, h = sizes[int(rng.integers(0, len(sizes)))]
+    if k % 2 == 0:
+        return layered_pair(seed=int(rng.integers(1 << 30)), width=w, height=h, channels=3,
+                            max_disp=150.0 * w / 1024.0)
+    m = max(2, int(0.03 * w))
+    shift = (int(rng.integers(-m, m + 1)), int(rng.integers(-m, m + 1)))
+    g = translation_pair(seed=int(rng.integers(1 << 30)), width=w, height=h, shift=shift,
+                         square=min(24, h // 4, w // 4),
+                         square_shift=(min(18, w // 8), min(11, h // 8)),
+                         rects=max(20, w * h // 4000))
+    return _gray_to_lab(g)
+
+
+def _batch_pair_args(a):
+    return batch_pair(*a)
+
+
+def make_batch(n: int = 64, seed: int = 4, sizes=BATCH_SIZES,
+               workers: int = 0) -> list[FramePair]:
+    """The n pairs of the mixed batch; `workers` > 1 generates them in a
+    process pool started with 'spawn' (safe after CUDA has been initialised)."""
+    args = [(seed, k, sizes) for k in range(n)]
+    if workers > 1 and n > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, n)) as pool:
+            return pool.map(_batch_pair_args, args)
+    return [batch_pair(*a) for a in args]
