@@ -13,6 +13,11 @@ ranks run independent replicas (the method does not shard within a pair).
 ``--schedule`` selects Flow Fields+ (Sec. 3.3), Fast or Fast x2 (Sec. 3.4)
 instead of the basic schedule; ``--two-way`` adds the second backward flow
 and the two-way check of Sec. 3.7 to every step.
+
+The line's ``batched`` object times the batched form (``ff_batch_run``, one
+CUDA graph per step, pairs overlapping in matching slots) on two batches:
+32 Sintel-shaped pairs (distinct seeds) and 64 pairs of mixed sizes
+(320x240, 640x480, 1024x436, 1242x375).
 """
 from __future__ import annotations
 
@@ -328,6 +333,60 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
 ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock (Tops/s)
 
 
+def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int) -> dict:
+    """Throughput of the batched form on `pairs` (inputs resident, L2
+    flushed between steps, one graph launch per step timed with CUDA events
+    on the batch's stream)."""
+    import torch
+
+    from paper_1703_02563_gb300 import ff
+
+    dev = torch.device("cuda", local_rank)
+    W = max(p.width for p in pairs)
+    H = max(p.height for p in pairs)
+    cfg = ff.Config(channels=prm["channels"], scales=prm["scales"], iters=prm["iters"],
+                    radius_q3=prm["radius_q3"], max_width=W, max_height=H)
+    stream = torch.cuda.Stream(dev)
+    b = ff.ff_batch_create(cfg, local_rank, slots=slots, stream=stream)
+    imgs = [(torch.from_numpy(p.img1).to(dev), torch.from_numpy(p.img2).to(dev)) for p in pairs]
+    outs = [tuple(torch.empty(s, dtype=t, device=dev)
+                  for s, t in (((p.height, p.width, 2), torch.int16),
+                               ((p.height, p.width, 2), torch.int16),
+                               ((p.height, p.width), torch.uint8))) for p in pairs]
+    descs = ff.pair_descs([dict(img1=i1, img2=i2, w=p.width, h=p.height, pair_id=k,
+                                flow_fwd=o[0], flow_bwd=o[1], mask=o[2])
+                           for k, (p, (i1, i2), o) in enumerate(zip(pairs, imgs, outs))])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        ff.ff_batch_run(b, descs, use_graph=True)
+    ff.ff_batch_sync(b)
+    n0 = ff.ff_batch_launch_count(b)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        ff.ff_batch_run(b, descs, use_graph=True)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ff.ff_batch_sync(b)
+    launches = ff.ff_batch_launch_count(b) - n0
+    ff.ff_batch_destroy(b)
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_s = sum(ms) / 1e3
+    evals = sum(2 * eval_count(p.width, p.height, cfg) for p in pairs) * steps
+    sweep_ops = sum(2 * sweep_evals(p.width, p.height, cfg) for p in pairs) * steps \
+        * 9 * prm["channels"] * 10
+    return {"value": len(pairs) * steps / total_s, "unit": "pairs/s", "pairs": len(pairs),
+            "slots": slots, "steps": steps, "ms_per_batch": total_s * 1e3 / steps,
+            "evals_per_s": evals / total_s, "gpu_launches": launches,
+            # a lower bound on k_sweep's ALU fraction: all of the step's time charged to it
+            "sweep_alu_frac_of_step": sweep_ops / total_s / 1e12 / ALU_PEAK_TOPS,
+            "sizes": sorted({f"{p.width}x{p.height}" for p in pairs})}
+
+
 def recorded_traffic(kernel: str) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if the kernel's
     sources are unchanged since it was taken."""
@@ -401,6 +460,9 @@ def main():
                          "fast_x2 (Sec. 3.3-3.4)")
     ap.add_argument("--two-way", action="store_true",
                     help="second backward flow and two-way check (Sec. 3.7)")
+    ap.add_argument("--batch-slots", type=int, default=32,
+                    help="matching slots of the batched legs (0 = skip them)")
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--sweep-warps", type=int, default=0,
                     help="propagation warps per sweep CTA (1, 2, 4; 0 = library default)")
     args = ap.parse_args()
@@ -440,11 +502,23 @@ def main():
         print(json.dumps(line))
         return
 
+    batches = {}
+    if args.batch_slots and args.schedule == "basic" and not args.two_way and world == 1:
+        # generated before CUDA starts, in a spawn pool
+        from paper_1703_02563_gb300 import workloads
+        workers = min(16, os.cpu_count() or 1)
+        batches["sintel1024x436_x32"] = (workloads.make_batch(
+            32, seed=2, sizes=((1024, 436),), workers=workers, layered_only=True),
+            workloads.BATCH_PARAMS)
+        batches["mixed64"] = (workloads.make_batch(64, seed=4, workers=workers),
+                              workloads.BATCH_PARAMS)
     if world > 1:
         import torch
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world, local_rank)
+    batched = {name: run_batched(pairs, prm, args.batch_slots, args.batch_steps, 3, local_rank)
+               for name, (pairs, prm) in batches.items()}
     total_s = res["total_ms"] / 1e3
     e2e_s = res["e2e_s"]
     if world > 1:
@@ -482,6 +556,8 @@ def main():
         "roofline": roofline(res, K, n_dirs),
         "kernels_ms": {k: round(v[1], 4) for k, v in res["kstats"].items() if v[0]},
     }
+    if batched:
+        line["batched"] = batched
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -500,14 +500,15 @@ def _gray_to_lab(pair: FramePair) -> FramePair:
                      pair.name + "-lab")
 
 
-def batch_pair(seed: int, k: int, sizes=BATCH_SIZES) -> FramePair:
+def batch_pair(seed: int, k: int, sizes=BATCH_SIZES, layered_only: bool = False) -> FramePair:
     """Pair k of the mixed batch: a size drawn uniformly from `sizes` and,
     alternately, the layered Sintel-shaped generator (displacement scaled to
     the frame: 150 px at 1024 wide) or the translation generator of the tiny
-    workload (a per-pair global shift up to 3 % of the width, promoted to Lab)."""
+    workload (a per-pair global shift up to 3 % of the width, promoted to Lab).
+    layered_only: every pair from the layered generator."""
     rng = np.random.default_rng([seed, k])
     w, h = sizes[int(rng.integers(0, len(sizes)))]
-    if k % 2 == 0:
+    if k % 2 == 0 or layered_only:
         return layered_pair(seed=int(rng.integers(1 << 30)), width=w, height=h, channels=3,
                             max_disp=150.0 * w / 1024.0)
     m = max(2, int(0.03 * w))
@@ -523,11 +524,11 @@ def _batch_pair_args(a):
     return batch_pair(*a)
 
 
-def make_batch(n: int = 64, seed: int = 4, sizes=BATCH_SIZES,
-               workers: int = 0) -> list[FramePair]:
+def make_batch(n: int = 64, seed: int = 4, sizes=BATCH_SIZES, workers: int = 0,
+               layered_only: bool = False) -> list[FramePair]:
     """The n pairs of the mixed batch; `workers` > 1 generates them in a
     process pool started with 'spawn' (safe after CUDA has been initialised)."""
-    args = [(seed, k, sizes) for k in range(n)]
+    args = [(seed, k, sizes, layered_only) for k in range(n)]
     if workers > 1 and n > 1:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(min(workers, n)) as pool:
