@@ -634,3 +634,57 @@ void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, i
     for (long i = 0; i < n; i++) mask[i] = (uint8_t)(mask[i] & m2[i]);
     free(m2);
 }
+
+/* Sec. 3.7, region filter.  Kept points (mask_in = 1) are segmented into
+ * regions: two 4-neighbours belong to the same region when their flows
+ * differ by less than 3 px (|F(p) - F(q)| < 24 in Q3; only neighbours'
+ * differences count, so a region's flow may drift).  A region of fewer than
+ * s points is removed when one of its points has a 4-neighbour that the
+ * consistency check removed (mask_in = 0, flow set) and that the same rule
+ * would join to it.  Regions are found by breadth-first search from each
+ * unvisited kept point in raster order. */
+static int close3(const int16_t *f, long a, long b) {
+    long dx = (long)f[2 * a] - f[2 * b], dy = (long)f[2 * a + 1] - f[2 * b + 1];
+    return dx * dx + dy * dy < 24L * 24L;
+}
+
+void ffo_region_filter(const int16_t *fwd, const uint8_t *mask_in, int W, int H, int s,
+                       uint8_t *mask_out) {
+    const long n = (long)W * H;
+    long *queue = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    long *region = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    uint8_t *seen = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    const int ox[4] = {1, -1, 0, 0}, oy[4] = {0, 0, 1, -1};
+    memcpy(mask_out, mask_in, (size_t)n);
+    for (long start = 0; start < n; start++) {
+        if (!mask_in[start] || seen[start]) continue;
+        long head = 0, tail = 0, size = 0;
+        int joins_outlier = 0;
+        queue[tail++] = start;
+        seen[start] = 1;
+        while (head < tail) {
+            long p = queue[head++];
+            region[size++] = p;
+            int x = (int)(p % W), y = (int)(p / W);
+            for (int k = 0; k < 4; k++) {
+                int qx = x + ox[k], qy = y + oy[k];
+                if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                long q = (long)qy * W + qx;
+                if (!close3(fwd, p, q)) continue;
+                if (mask_in[q]) {
+                    if (!seen[q]) {
+                        seen[q] = 1;
+                        queue[tail++] = q;
+                    }
+                } else if (fwd[2 * q] != INVALID_F && fwd[2 * q + 1] != INVALID_F) {
+                    joins_outlier = 1;
+                }
+            }
+        }
+        if (size < s && joins_outlier)
+            for (long i = 0; i < size; i++) mask_out[region[i]] = 0;
+    }
+    free(queue);
+    free(region);
+    free(seen);
+}

@@ -125,6 +125,13 @@ void ffo_filter_grid(const int16_t *fwd, const int16_t *bwd, int WL, int HL, int
 void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, int WL, int HL,
                  int L, int eps_q3, uint8_t *mask);
 
+/* Sec. 3.7 region filter on a grid [H][W]: mask_out = mask_in minus every
+ * region (4-neighbours with flows less than 3 px apart) of fewer than s
+ * points that the same rule would join to a point the consistency check
+ * removed (mask_in = 0, flow set). */
+void ffo_region_filter(const int16_t *fwd, const uint8_t *mask_in, int W, int H, int s,
+                       uint8_t *mask_out);
+
 #ifdef __cplusplus
 }
 #endif

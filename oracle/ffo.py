@@ -50,6 +50,8 @@ def lib():
         L.ffo_match.restype = i
         L.ffo_filter.argtypes = [P, P, i, i, i, P]
         L.ffo_filter_grid.argtypes = [P, P, i, i, i, i, P]
+        L.ffo_region_filter.argtypes = [P, P, i, i, i, P]
+        L.ffo_region_filter.restype = None
         L.ffo_filter2.argtypes = [P, P, P, i, i, i, i, P]
         L.ffo_schedule_final_level.argtypes = [i]
         L.ffo_schedule_final_level.restype = i
@@ -302,3 +304,13 @@ def filter_mask2(fwd: np.ndarray, bwd1: np.ndarray, bwd2: np.ndarray, eps_q3: in
     mask = np.zeros((H, W), np.uint8)
     lib().ffo_filter2(_p(fwd), _p(bwd1), _p(bwd2), W, H, level, eps_q3, _p(mask))
     return mask
+
+
+def region_filter(fwd: np.ndarray, mask: np.ndarray, s: int) -> np.ndarray:
+    """Region filter (Sec. 3.7) of a consistency mask on the flows' grid."""
+    fwd = np.ascontiguousarray(fwd, np.int16)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    H, W, _ = fwd.shape
+    out = np.zeros((H, W), np.uint8)
+    lib().ffo_region_filter(_p(fwd), _p(mask), W, H, s, _p(out))
+    return out

@@ -669,3 +669,93 @@ def test_grid_filter_is_the_pixel_filter_on_block_constant_flows():
     grid = O.filter_mask(fwd[::2, ::2], bwd[::2, ::2], 12, level=1)
     assert 0 < grid.sum() < grid.size
     np.testing.assert_array_equal(grid, full[::2, ::2])
+
+
+# --------------------------------------------------------------------------
+# region filter (Sec. 3.7)
+# --------------------------------------------------------------------------
+def _region_filter_by_graph(fwd, mask, s):
+    """The rule restated with networkx's connected components."""
+    nx = pytest.importorskip("networkx")
+    H, W, _ = fwd.shape
+    f = fwd.astype(np.int64)
+    close = lambda a, b: ((f[a] - f[b]) ** 2).sum() < 24 * 24
+    g = nx.Graph()
+    for y in range(H):
+        for x in range(W):
+            if mask[y, x]:
+                g.add_node((y, x))
+    for y in range(H):
+        for x in range(W):
+            for yy, xx in ((y, x + 1), (y + 1, x)):
+                if yy < H and xx < W and mask[y, x] and mask[yy, xx] and close((y, x), (yy, xx)):
+                    g.add_edge((y, x), (yy, xx))
+    out = mask.copy()
+    for comp in nx.connected_components(g):
+        if len(comp) >= s:
+            continue
+        joinable = False
+        for (y, x) in comp:
+            for yy, xx in ((y, x + 1), (y, x - 1), (y + 1, x), (y - 1, x)):
+                if 0 <= yy < H and 0 <= xx < W and not mask[yy, xx] \
+                        and fwd[yy, xx, 0] != -32768 and close((y, x), (yy, xx)):
+                    joinable = True
+        if joinable:
+            for (y, x) in comp:
+                out[y, x] = 0
+    return out
+
+
+def test_region_filter_worked_examples():
+    row = lambda fx: np.array([[[v, 0] for v in fx]], np.int16)
+    m = np.array([[1, 1, 1, 1, 1, 0]], np.uint8)
+    # pixels 3-4 form a 2-pixel region whose removed neighbour 5 is far: kept
+    f = row([0, 0, 0, 100, 100, 0])
+    np.testing.assert_array_equal(O.region_filter(f, m, 3), m)
+    # the removed neighbour is 2 px away from pixel 4: the region is removed
+    f = row([0, 0, 0, 100, 100, 116])
+    np.testing.assert_array_equal(O.region_filter(f, m, 3)[0], [1, 1, 1, 0, 0, 0])
+    # ... unless it is not smaller than s
+    np.testing.assert_array_equal(O.region_filter(f, m, 2), m)
+    # exactly 3 px apart is not "below 3 pixels": pixels 3 and 4 split, and
+    # only the single pixel 4 joins the outlier
+    f = row([0, 0, 0, 100, 124, 140])
+    np.testing.assert_array_equal(O.region_filter(f, m, 3)[0], [1, 1, 1, 1, 0, 0])
+    # an unset flow joins nothing
+    f = row([0, 0, 0, 100, 100, -32768])
+    np.testing.assert_array_equal(O.region_filter(f, m, 3), m)
+    # diagonal neighbours do not connect: the 1-pixel region at (1, 1) has
+    # only a diagonal removed neighbour, and stays
+    f = np.zeros((2, 2, 2), np.int16)
+    only_11 = np.array([[0, 0], [0, 1]], np.uint8)
+    # (0, 1) and (1, 0) are removed 4-neighbours with the same flow: removed
+    np.testing.assert_array_equal(O.region_filter(f, only_11, 5), [[0, 0], [0, 0]])
+    # with those two unset, only the diagonal (0, 0) remains: kept
+    f[0, 1] = f[1, 0] = (-32768, -32768)
+    np.testing.assert_array_equal(O.region_filter(f, only_11, 5), only_11)
+
+
+def test_region_filter_drifting_region_counts_whole():
+    # flows rising 2 px per pixel: one region of 10 (neighbours close, ends
+    # 18 px apart); with s = 10 it is not small, with s = 11 it is
+    f = np.array([[[16 * i, 0] for i in range(10)] + [[16 * 9 + 8, 0]]], np.int16)
+    m = np.array([[1] * 10 + [0]], np.uint8)
+    np.testing.assert_array_equal(O.region_filter(f, m, 10), m)
+    np.testing.assert_array_equal(O.region_filter(f, m, 11)[0], [0] * 11)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_region_filter_equals_connected_components(seed):
+    rng = np.random.default_rng(seed)
+    H, W = 23, 31
+    blocks = rng.integers(-6, 7, (H // 4 + 1, W // 4 + 1, 2)) * 20
+    f = np.repeat(np.repeat(blocks, 4, 0), 4, 1)[:H, :W] + rng.integers(-14, 15, (H, W, 2))
+    f = f.astype(np.int16)
+    f[rng.random((H, W)) < 0.05] = (-32768, -32768)
+    m = (rng.random((H, W)) < 0.8).astype(np.uint8)
+    m[f[..., 0] == -32768] = 0
+    for s in (1, 4, 15, 60):
+        got = O.region_filter(f, m, s)
+        np.testing.assert_array_equal(got, _region_filter_by_graph(f, m, s), err_msg=f"s {s}")
+        assert np.all(got <= m)
+    assert (O.region_filter(f, m, 60) != m).any()
