@@ -92,6 +92,8 @@ typedef struct {
     int max_width;    /* largest frame the context must hold, 1..4096                     */
     int max_height;
     int schedule;     /* an ff_schedule value                                             */
+    int region_min;   /* s of the region filter (Sec. 3.7) applied after the consistency  */
+                      /* check by ff_pair_host and ff_batch_run; 0 = off (default)        */
 } ff_config;
 
 /* Fills the paper's defaults: patch 8, 9 coefficients, 1 channel, S = 4,
@@ -150,9 +152,21 @@ ff_status ff_filter(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_bw
 ff_status ff_filter_2way(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_bwd1,
                          const int16_t *flow_bwd2, uint8_t *mask_out);
 
+/* Sec. 3.7 region filter.  Kept points of mask_in are segmented into
+ * regions: 4-neighbours whose forward flows differ by less than 3 px
+ * (squared Q3 distance < 24^2) share a region.  A region of fewer than
+ * min_region points is deleted when one of its points has a 4-neighbour that
+ * mask_in rejects, whose flow is set, and that the same rule would join to
+ * it.  flow_fwd: int16 final grid [..][..][2]; mask_in / mask_out: uint8 on
+ * the same grid (they may be the same buffer).  Uses context scratch, so
+ * calls on one context run in stream order. */
+ff_status ff_region_filter(ff_ctx *ctx, const int16_t *flow_fwd, const uint8_t *mask_in,
+                           int min_region, uint8_t *mask_out);
+
 /* Whole pair with HOST buffers (blocking): copies both frames in (planar
  * uint8 [channels][h][w]), builds features, matches forward and backward
- * concurrently, filters, and copies the results out: flow_fwd_host and
+ * concurrently, filters (and region-filters when cfg.region_min > 0), and
+ * copies the results out: flow_fwd_host and
  * flow_bwd_host int16 [h][w][2], mask_host uint8 [h][w] (on the final grid
  * of the schedule; any may be NULL to skip its copy).  Pinned host memory makes the copies asynchronous.
  * Returns after the results are on the host. */
@@ -220,7 +234,7 @@ ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
  * 0) stops.  ff_kernel_stats (call after ff_sync) returns, for the kernel
  * named `kernel` ("k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge",
  * "k_seed_rerank", "k_seed_given", "k_upsample", "k_sweep", "k_export",
- * "k_filter", "k_dense"), the number of recorded launches and their summed
+ * "k_filter", "k_dense", "k_region"), the number of recorded launches and their summed
  * device time in milliseconds. */
 ff_status ff_profile(ff_ctx *ctx, int enable);
 ff_status ff_kernel_stats(ff_ctx *ctx, const char *kernel, long long *launches,

@@ -326,6 +326,91 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
 #include "ff_sweep.cuh"
 #include "ff_seed.cuh"
 
+// ---- region filter (Sec. 3.7) ------------------------------------------
+// Kept points are joined into regions by a lock-free union-find: a root only
+// ever gets a smaller parent (atomicMin), so every tree's root is the
+// smallest index of its region and no thread waits on another.
+__device__ __forceinline__ bool rf_close(uint32_t a, uint32_t b) {
+    const int dx = flow_x(a) - flow_x(b), dy = flow_y(a) - flow_y(b);
+    return dx * dx + dy * dy < 24 * 24;   // below 3 px
+}
+
+__device__ __forceinline__ int rf_find(const int *parent, int x) {
+    int p;
+    while ((p = __ldcg(parent + x)) != x) x = p;
+    return x;
+}
+
+__device__ void rf_unite(int *parent, int a, int b) {
+    for (;;) {
+        a = rf_find(parent, a);
+        b = rf_find(parent, b);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(parent + b, a);   // link the larger root under the smaller
+        if (old == b) return;
+        b = old;                                     // b got another parent meanwhile: retry
+    }
+}
+
+__global__ void k_rf_init(const uint8_t *__restrict__ mask, int N, int *parent, int *size,
+                          uint8_t *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    parent[i] = mask[i] ? i : -1;
+    size[i] = 0;
+    flag[i] = 0;
+}
+
+__global__ void k_rf_union(const uint32_t *__restrict__ flow, const uint8_t *__restrict__ mask,
+                           int W, int H, int *parent) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H || !mask[i]) return;
+    const int y = i / W, x = i - y * W;
+    const uint32_t f = flow[i];
+    if (x + 1 < W && mask[i + 1] && rf_close(f, flow[i + 1])) rf_unite(parent, i, i + 1);
+    if (y + 1 < H && mask[i + W] && rf_close(f, flow[i + W])) rf_unite(parent, i, i + W);
+}
+
+// region sizes, and whether a region touches a joinable removed point
+__global__ void k_rf_count(const uint32_t *__restrict__ flow, const uint8_t *__restrict__ mask,
+                           int W, int H, int *parent, int *size, uint8_t *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H || !mask[i]) return;
+    const int y = i / W, x = i - y * W;
+    const int r = rf_find(parent, i);
+    parent[i] = r;
+    atomicAdd(size + r, 1);
+    const uint32_t f = flow[i];
+    const int nb[4] = {x + 1 < W ? i + 1 : -1, x > 0 ? i - 1 : -1, y + 1 < H ? i + W : -1,
+                       y > 0 ? i - W : -1};
+    bool join = false;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (nb[k] < 0 || mask[nb[k]]) continue;
+        const uint32_t g = flow[nb[k]];
+        if (flow_x(g) != -32768 && flow_y(g) != -32768 && rf_close(f, g)) join = true;
+    }
+    if (join) flag[r] = 1;
+}
+
+__global__ void k_rf_apply(const uint8_t *mask_in, int N, int s, const int *__restrict__ parent,
+                           const int *__restrict__ size, const uint8_t *__restrict__ flag,
+                           uint8_t *mask_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    uint8_t m = mask_in[i];
+    if (m) {
+        const int r = parent[i];
+        if (size[r] < s && flag[r]) m = 0;
+    }
+    mask_out[i] = m;
+}
+
 // level state -> caller's flow / cost arrays
 __global__ void k_export(const uint32_t *__restrict__ flow, const int *__restrict__ cost, int N,
                          uint32_t *__restrict__ flow_out, int *__restrict__ cost_out) {
@@ -417,6 +502,9 @@ struct ff_ctx {
     uint8_t *img_dev[2] = {nullptr, nullptr};
     uint32_t *pair_flow[2] = {nullptr, nullptr};
     uint8_t *pair_mask = nullptr;
+    // region filter scratch: union-find parents, region sizes, join flags
+    int *rf_parent = nullptr, *rf_size = nullptr;
+    uint8_t *rf_flag = nullptr;
     unsigned long long wait_ns = 2000000000ull;
     int sweep_warps = 1;   // propagation warps per sweep CTA: 1, 2 or 4
     int force_timeout = 0;
@@ -455,7 +543,7 @@ ff_status check_cuda(ff_ctx *ctx, cudaError_t e, const char *what) {
 
 const char *const kKernelNames[] = {"k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge",
                                     "k_seed_rerank", "k_seed_given", "k_upsample",
-                                    "k_sweep", "k_export", "k_filter", "k_dense"};
+                                    "k_sweep", "k_export", "k_filter", "k_dense", "k_region"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 int kernel_id(const char *name) {
@@ -551,6 +639,9 @@ void free_all(ff_ctx *c) {
         cudaFree(d.err);
     }
     cudaFree(c->pair_mask);
+    cudaFree(c->rf_parent);
+    cudaFree(c->rf_size);
+    cudaFree(c->rf_flag);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
     if (c->side) cudaStreamDestroy(c->side);
@@ -572,6 +663,8 @@ ff_status validate_config(const ff_config *c, std::string *why) {
     if (c->eps_q3 < 0 || c->eps_q3 > 65535) return *why = "eps_q3 out of range", FF_EINVAL;
     if (c->schedule < FF_SCHED_BASIC || c->schedule > FF_SCHED_PLUS_FAST_X2)
         return *why = "unknown schedule", FF_EINVAL;
+    if (c->region_min < 0 || c->region_min > (1 << 24))
+        return *why = "region_min out of range", FF_EINVAL;
     if (c->schedule == FF_SCHED_PLUS_FAST_X2 && c->scales < 2)
         return *why = "the Fast x2 schedule needs at least 2 scales", FF_EINVAL;
     if (c->max_width < 1 || c->max_width > FF_MAX_DIM || c->max_height < 1 ||
@@ -861,6 +954,8 @@ ff_status run_match(ff_ctx *c, ff_dir dir, uint32_t pair_id, const int16_t *seed
 
 ff_status filter_into(ff_ctx *c, const int16_t *fwd, const int16_t *b1, const int16_t *b2,
                       uint8_t *mask);
+ff_status region_into(ff_ctx *c, const int16_t *fwd, const uint8_t *mask_in, int s,
+                      uint8_t *mask_out);
 
 // One whole pair on device buffers, enqueued without waiting: features on
 // the context's stream, the backward flow(s) on the side stream(s)
@@ -895,7 +990,9 @@ ff_status enqueue_pair(ff_ctx *c, const uint8_t *img1, const uint8_t *img2, int 
         if ((s = check_cuda(c, cudaEventRecord(c->ev_c, c->side2), "event"))) return s;
         if ((s = check_cuda(c, cudaStreamWaitEvent(main, c->ev_c, 0), "wait"))) return s;
     }
-    if (mask) return filter_into(c, fwd, bwd, bwd2, mask);
+    if (!mask) return FF_OK;
+    if ((s = filter_into(c, fwd, bwd, bwd2, mask))) return s;
+    if (c->cfg.region_min > 0) return region_into(c, fwd, mask, c->cfg.region_min, mask);
     return FF_OK;
 }
 
@@ -931,6 +1028,30 @@ ff_status filter_into(ff_ctx *c, const int16_t *fwd, const int16_t *b1, const in
         k_filter<1><<<(N + 255) / 256, 256, 0, c->stream>>>(
             (const uint32_t *)fwd, (const uint32_t *)b1, nullptr, W, H, Lf, c->cfg.eps_q3, mask);
     return check_launch(c, "k_filter");
+}
+
+// Sec. 3.7 region filter on the final grid (mask_in may equal mask_out)
+ff_status region_into(ff_ctx *c, const int16_t *fwd, const uint8_t *mask_in, int s,
+                      uint8_t *mask_out) {
+    const int Lf = final_level(c->cfg);
+    int W, H;
+    level_dims(c->fw[0], c->fh[0], Lf, &W, &H);
+    const int N = W * H, nb = (N + 255) / 256;
+    const uint32_t *f = (const uint32_t *)fwd;
+    ff_status st;
+    prof_begin(c, "k_region");
+    k_rf_init<<<nb, 256, 0, c->stream>>>(mask_in, N, c->rf_parent, c->rf_size, c->rf_flag);
+    if ((st = check_launch(c, "k_region"))) return st;
+    prof_begin(c, "k_region");
+    k_rf_union<<<nb, 256, 0, c->stream>>>(f, mask_in, W, H, c->rf_parent);
+    if ((st = check_launch(c, "k_region"))) return st;
+    prof_begin(c, "k_region");
+    k_rf_count<<<nb, 256, 0, c->stream>>>(f, mask_in, W, H, c->rf_parent, c->rf_size, c->rf_flag);
+    if ((st = check_launch(c, "k_region"))) return st;
+    prof_begin(c, "k_region");
+    k_rf_apply<<<nb, 256, 0, c->stream>>>(mask_in, N, s, c->rf_parent, c->rf_size, c->rf_flag,
+                                          mask_out);
+    return check_launch(c, "k_region");
 }
 
 }  // namespace
@@ -1044,6 +1165,9 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
         if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int));
     }
     if (e == cudaSuccess) e = alloc(&c->pair_mask, npix);
+    if (e == cudaSuccess) e = alloc(&c->rf_parent, npix);
+    if (e == cudaSuccess) e = alloc(&c->rf_size, npix);
+    if (e == cudaSuccess) e = alloc(&c->rf_flag, npix);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming);
@@ -1134,6 +1258,18 @@ ff_status ff_filter_2way(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow
     if (s) return s;
     DeviceGuard guard(c->device);
     return filter_into(c, flow_fwd, flow_bwd1, flow_bwd2, mask_out);
+}
+
+ff_status ff_region_filter(ff_ctx *c, const int16_t *flow_fwd, const uint8_t *mask_in,
+                           int min_region, uint8_t *mask_out) {
+    if (!c) return FF_EINVAL;
+    if (!flow_fwd || !mask_in || !mask_out) return fail(c, FF_EINVAL, "NULL argument");
+    if ((uintptr_t)flow_fwd & 3) return fail(c, FF_EINVAL, "flow must be 4-byte aligned");
+    if (min_region < 0) return fail(c, FF_EINVAL, "min_region < 0");
+    ff_status s = check_pair(c);
+    if (s) return s;
+    DeviceGuard guard(c->device);
+    return region_into(c, flow_fwd, mask_in, min_region, mask_out);
 }
 
 ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_host, int w,

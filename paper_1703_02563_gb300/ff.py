@@ -22,7 +22,7 @@ FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS = 1, 2, 3
 INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
-            "ff_match_until", "ff_filter", "ff_filter_2way", "ff_pair_host", "ff_get_features", "ff_seed_knn",
+            "ff_match_until", "ff_filter", "ff_filter_2way", "ff_region_filter", "ff_pair_host", "ff_get_features", "ff_seed_knn",
             "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
             "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy",
             "ff_batch_create", "ff_batch_run", "ff_batch_set_stream", "ff_batch_sync",
@@ -34,7 +34,7 @@ class ff_config(ct.Structure):
                 ("scales", ct.c_int), ("iters", ct.c_int), ("radius_q3", ct.c_int),
                 ("seed_leaf", ct.c_int), ("seed_stride", ct.c_int), ("eps_q3", ct.c_int),
                 ("seed", ct.c_uint32), ("max_width", ct.c_int), ("max_height", ct.c_int),
-                ("schedule", ct.c_int)]
+                ("schedule", ct.c_int), ("region_min", ct.c_int)]
 
 
 class ff_pair_desc(ct.Structure):
@@ -67,6 +67,7 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_match_until.argtypes = [P, i, u32, P, i, i, P, P]
         L.ff_filter.argtypes = [P, P, P, P]
         L.ff_filter_2way.argtypes = [P, P, P, P, P]
+        L.ff_region_filter.argtypes = [P, P, P, i, P]
         L.ff_pair_host.argtypes = [P, P, P, i, i, u32, P, P, P]
         L.ff_get_features.argtypes = [P, i, i, P]
         L.ff_seed_knn.argtypes = [P, i, P, P]
@@ -144,6 +145,7 @@ class Config:
     patch: int = 8
     n_coeffs: int = 9
     schedule: int = FF_SCHED_BASIC
+    region_min: int = 0
 
     def final_level(self) -> int:
         """The grid the schedule's matches come on (1 for Fast x2, else 0)."""
@@ -220,6 +222,11 @@ def ff_filter_2way(ctx: int, flow_fwd, flow_bwd1, flow_bwd2, mask_out) -> None:
                                      _ptr(mask_out)))
 
 
+def ff_region_filter(ctx: int, flow_fwd, mask_in, min_region: int, mask_out) -> None:
+    _check(ctx, lib().ff_region_filter(ctx, _ptr(flow_fwd), _ptr(mask_in), min_region,
+                                       _ptr(mask_out)))
+
+
 def ff_pair_host(ctx: int, img1_host, img2_host, w: int, h: int, pair_id: int,
                  flow_fwd_host=None, flow_bwd_host=None, mask_host=None) -> None:
     _check(ctx, lib().ff_pair_host(ctx, _ptr(img1_host), _ptr(img2_host), w, h, pair_id,
@@ -266,7 +273,7 @@ def ff_kernel_stats(ctx: int, kernel: str) -> tuple[int, float]:
 
 
 KERNELS = ("k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge", "k_seed_rerank", "k_seed_given",
-           "k_upsample", "k_sweep", "k_export", "k_filter", "k_dense")
+           "k_upsample", "k_sweep", "k_export", "k_filter", "k_dense", "k_region")
 
 
 def ff_launch_count(ctx: int) -> int:
@@ -355,6 +362,11 @@ class Context:
         mask = torch.empty((HL, WL), dtype=torch.uint8, device=flow_fwd.device)
         ff_filter_2way(self.ctx, flow_fwd, flow_bwd1, flow_bwd2, mask)
         return mask
+
+    def region_filter(self, flow_fwd, mask, min_region: int):
+        out = self.torch.empty_like(mask)
+        ff_region_filter(self.ctx, flow_fwd, mask, min_region, out)
+        return out
 
     def features_of(self, slot: int, level: int):
         torch = self.torch
