@@ -142,7 +142,7 @@ def measured_peaks() -> dict:
 # ----------------------------------------------------------------------------
 # CPU oracle (the baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def cpu_oracle_rate(pair, prm, schedule: int = 0, two_way: bool = False,
+def cpu_oracle_rate(pair, prm, schedule: int = 0, two_way: bool = False, region: int = 0,
                     budget_rows: int = 6) -> dict:
     """Time the oracle, as it stands, on a bounded sample of one pair.
 
@@ -182,9 +182,11 @@ def cpu_oracle_rate(pair, prm, schedule: int = 0, two_way: bool = False,
     t0 = time.perf_counter()
     Lf = P.final_level()
     if two_way:
-        O.filter_mask2(flows[0], flows[1], flows[2], 8, level=Lf)
+        mask = O.filter_mask2(flows[0], flows[1], flows[2], 8, level=Lf)
     else:
-        O.filter_mask(flows[0], flows[1], 8, level=Lf)
+        mask = O.filter_mask(flows[0], flows[1], 8, level=Lf)
+    if region:
+        O.region_filter(flows[0], mask, region)
     t_filt = time.perf_counter() - t0
     wall = time.perf_counter() - t_all
     per_pair = t_feat + t_seed + t_prop + t_filt
@@ -212,7 +214,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     W, H = pair.width, pair.height
     schedule = SCHEDULES[args.schedule]
     cfg = ff.Config(channels=C, scales=S, iters=I, radius_q3=R, max_width=W, max_height=H,
-                    schedule=schedule, seed_stride=2 if args.schedule == "fast_x2" else 1)
+                    schedule=schedule, seed_stride=2 if args.schedule == "fast_x2" else 1,
+                    region_min=args.region)
     WL, HL = level_dims(W, H, cfg.final_level())
     main = torch.cuda.Stream(dev)
     side = torch.cuda.Stream(dev)
@@ -255,6 +258,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
             ff.ff_filter_2way(ctx, flow_f, flow_b, flow_b2, mask)
         else:
             ff.ff_filter(ctx, flow_f, flow_b, mask)
+        if args.region:
+            ff.ff_region_filter(ctx, flow_f, mask, args.region, mask)
 
     for i in range(args.warmup):
         step(i)
@@ -460,6 +465,8 @@ def main():
                          "fast_x2 (Sec. 3.3-3.4)")
     ap.add_argument("--two-way", action="store_true",
                     help="second backward flow and two-way check (Sec. 3.7)")
+    ap.add_argument("--region", type=int, default=0,
+                    help="region filter s (Sec. 3.7) after the consistency check; 0 = off")
     ap.add_argument("--batch-slots", type=int, default=32,
                     help="matching slots of the batched legs (0 = skip them)")
     ap.add_argument("--batch-steps", type=int, default=5)
@@ -481,7 +488,7 @@ def main():
         rates = []
         sample = None
         for _ in range(max(1, args.steps)):
-            r = cpu_oracle_rate(pair, prm, SCHEDULES[args.schedule], args.two_way,
+            r = cpu_oracle_rate(pair, prm, SCHEDULES[args.schedule], args.two_way, args.region,
                                 budget_rows=2)
             rates.append(r["pairs_per_s"])
             sample = r["sample"]
@@ -545,7 +552,7 @@ def main():
         "config": {"workload": args.workload, "frame": f"{W}x{H}", "channels": C, "scales": S,
                    "iters": I, "radius_q3": res["prm"]["radius_q3"], "seed_leaf": 8,
                    "schedule": args.schedule, "seed_stride": res["cfg"].seed_stride,
-                   "backward_flows": n_dirs - 1,
+                   "backward_flows": n_dirs - 1, "region_min": args.region,
                    "l2": "flushed between steps (256 MiB write outside the step events)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "clocks": res["clocks"],
@@ -562,7 +569,8 @@ def main():
         import torch
         torch.distributed.destroy_process_group()
     if not args.no_cpu_baseline and world == 1:
-        r = cpu_oracle_rate(res["pair"], res["prm"], SCHEDULES[args.schedule], args.two_way)
+        r = cpu_oracle_rate(res["pair"], res["prm"], SCHEDULES[args.schedule], args.two_way,
+                            args.region)
         line["cpu_baseline"] = {"value": r["pairs_per_s"], "unit": "pairs/s",
                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
                                 "wall_s": round(r["wall_s"], 2)}
