@@ -19,7 +19,7 @@ def build(force: bool = False) -> str:
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra",
-           "-o", tmp, SRC, "-lpthread"]
+           "-ffp-contract=off", "-o", tmp, SRC, "-lpthread", "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

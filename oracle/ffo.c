@@ -21,6 +21,7 @@
 #include "ffo.h"
 
 #include <limits.h>
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -687,4 +688,53 @@ void ffo_region_filter(const int16_t *fwd, const uint8_t *mask_in, int W, int H,
     free(queue);
     free(region);
     free(seen);
+}
+
+/* Sec. 3.7-3.8 sparsification.  The grid is cut into q x q cells from the
+ * origin (the last row and column of cells may be partial).  A cell that
+ * still holds at least e kept points (mask_in = 1) keeps exactly one: the
+ * point whose consistency errors |F(p) + F_b(p + F(p))|, summed over the
+ * given backward flows (bwd2 may be NULL), are smallest; ties go to the
+ * first point in raster order.  Errors are Euclidean lengths in 1/8 px,
+ * each an IEEE double square root, summed in the order bwd1, bwd2.  The
+ * backward flows are read at the grid point nearest to p + F(p), as in the
+ * consistency check on the level-L grid; an unset flow or a target off the
+ * grid (possible only for masks not made by the check) counts as infinite. */
+static double check_error(const int16_t *fwd, const int16_t *bwd, int WL, int HL, int L, long i) {
+    const int n = 1 << L;
+    const int x = (int)(i % WL), y = (int)(i / WL);
+    const int Fx = fwd[2 * i], Fy = fwd[2 * i + 1];
+    if (Fx == INVALID_F || Fy == INVALID_F) return HUGE_VAL;
+    const int qx = x + floor_div(Fx + 4 * n, 8 * n), qy = y + floor_div(Fy + 4 * n, 8 * n);
+    if (qx < 0 || qx >= WL || qy < 0 || qy >= HL) return HUGE_VAL;
+    const long j = (long)qy * WL + qx;
+    const int Bx = bwd[2 * j], By = bwd[2 * j + 1];
+    if (Bx == INVALID_F || By == INVALID_F) return HUGE_VAL;
+    const long dx = (long)Fx + Bx, dy = (long)Fy + By;
+    return sqrt((double)(dx * dx + dy * dy));
+}
+
+void ffo_sparsify(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2,
+                  const uint8_t *mask_in, int WL, int HL, int L, int q, int e,
+                  uint8_t *mask_out) {
+    memset(mask_out, 0, (size_t)WL * HL);
+    for (int cy = 0; cy < HL; cy += q)
+        for (int cx = 0; cx < WL; cx += q) {
+            int count = 0;
+            long best = -1;
+            double best_err = 0.0;
+            for (int y = cy; y < cy + q && y < HL; y++)
+                for (int x = cx; x < cx + q && x < WL; x++) {
+                    const long i = (long)y * WL + x;
+                    if (!mask_in[i]) continue;
+                    count++;
+                    double err = check_error(fwd, bwd1, WL, HL, L, i);
+                    if (bwd2) err = err + check_error(fwd, bwd2, WL, HL, L, i);
+                    if (best < 0 || err < best_err) {
+                        best = i;
+                        best_err = err;
+                    }
+                }
+            if (count >= e && best >= 0) mask_out[best] = 1;
+        }
 }

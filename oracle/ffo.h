@@ -132,6 +132,13 @@ void ffo_filter2(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2, i
 void ffo_region_filter(const int16_t *fwd, const uint8_t *mask_in, int W, int H, int s,
                        uint8_t *mask_out);
 
+/* Sec. 3.7-3.8 sparsification on the level-L grid [HL][WL]: in each q x q
+ * cell with at least e kept points, keep the one with the smallest summed
+ * consistency error over bwd1 and bwd2 (NULL: bwd1 only). */
+void ffo_sparsify(const int16_t *fwd, const int16_t *bwd1, const int16_t *bwd2,
+                  const uint8_t *mask_in, int WL, int HL, int L, int q, int e,
+                  uint8_t *mask_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,8 @@ def lib():
         L.ffo_filter_grid.argtypes = [P, P, i, i, i, i, P]
         L.ffo_region_filter.argtypes = [P, P, i, i, i, P]
         L.ffo_region_filter.restype = None
+        L.ffo_sparsify.argtypes = [P, P, P, P, i, i, i, i, i, P]
+        L.ffo_sparsify.restype = None
         L.ffo_filter2.argtypes = [P, P, P, i, i, i, i, P]
         L.ffo_schedule_final_level.argtypes = [i]
         L.ffo_schedule_final_level.restype = i
@@ -313,4 +315,18 @@ def region_filter(fwd: np.ndarray, mask: np.ndarray, s: int) -> np.ndarray:
     H, W, _ = fwd.shape
     out = np.zeros((H, W), np.uint8)
     lib().ffo_region_filter(_p(fwd), _p(mask), W, H, s, _p(out))
+    return out
+
+
+def sparsify(fwd: np.ndarray, bwd1: np.ndarray, bwd2: np.ndarray | None, mask: np.ndarray,
+             q: int, e: int, level: int = 0) -> np.ndarray:
+    """Sparsification (Sec. 3.7-3.8): one point per q x q cell of >= e kept points."""
+    fwd = np.ascontiguousarray(fwd, np.int16)
+    bwd1 = np.ascontiguousarray(bwd1, np.int16)
+    b2 = None if bwd2 is None else np.ascontiguousarray(bwd2, np.int16)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    H, W, _ = fwd.shape
+    out = np.zeros((H, W), np.uint8)
+    lib().ffo_sparsify(_p(fwd), _p(bwd1), None if b2 is None else _p(b2), _p(mask), W, H, level,
+                       q, e, _p(out))
     return out

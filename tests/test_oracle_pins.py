@@ -759,3 +759,55 @@ def test_region_filter_equals_connected_components(seed):
         np.testing.assert_array_equal(got, _region_filter_by_graph(f, m, s), err_msg=f"s {s}")
         assert np.all(got <= m)
     assert (O.region_filter(f, m, 60) != m).any()
+
+
+# --------------------------------------------------------------------------
+# sparsification (Sec. 3.7-3.8)
+# --------------------------------------------------------------------------
+def test_sparsify_worked_examples():
+    fwd = np.zeros((2, 2, 2), np.int16)
+    b1 = np.array([[[3, 4], [0, 4]], [[4, 0], [5, 12]]], np.int16)   # errors 5, 4, 4, 13
+    m = np.ones((2, 2), np.uint8)
+    # smallest error 4 twice: the first in raster order wins
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 2, 1), [[0, 1], [0, 0]])
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 2, 4), [[0, 1], [0, 0]])
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 2, 5), np.zeros((2, 2)))
+    # two backward flows: the errors add (5 + 0, 4 + 3, 4 + 5, 13 + 0)
+    b2 = np.array([[[0, 0], [3, 0]], [[3, 4], [0, 0]]], np.int16)
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, b2, m, 2, 1), [[1, 0], [0, 0]])
+    # a rejected point is never chosen
+    m2 = m.copy()
+    m2[0, 1] = 0
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m2, 2, 3), [[0, 0], [1, 0]])
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m2, 2, 4), np.zeros((2, 2)))
+
+
+def test_sparsify_partial_cells_and_trivial_cells():
+    rng = np.random.default_rng(5)
+    H, W = 7, 11
+    fwd = rng.integers(-3, 4, (H, W, 2)).astype(np.int16)
+    b1 = rng.integers(-9, 10, (H, W, 2)).astype(np.int16)
+    m = (rng.random((H, W)) < 0.7).astype(np.uint8)
+    # q = 1, e = 1: every kept point is its own cell
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 1, 1), m)
+    # q = 3: cells of 3 x 3, the last column of cells 2 wide, the last row 1 high
+    for e in (1, 3, 5):
+        out = O.sparsify(fwd, b1, None, m, 3, e)
+        assert np.all(out <= m)
+        for cy in range(0, H, 3):
+            for cx in range(0, W, 3):
+                cell_m = m[cy:cy + 3, cx:cx + 3]
+                cell_o = out[cy:cy + 3, cx:cx + 3]
+                assert cell_o.sum() == (1 if cell_m.sum() >= e else 0)
+
+
+def test_sparsify_level1_reads_the_nearest_grid_point():
+    # the backward flow is read where the grid consistency check reads it:
+    # on the level-1 grid F = (4, 0) stays at point 0 (error |4 + 20|) and
+    # F = (-4, 0) at point 1 (error |-4 - 4|); on the pixel grid F = (4, 0)
+    # reaches pixel 1 (error |4 - 4| = 0)
+    fwd = np.array([[[4, 0], [-4, 0]]], np.int16)
+    b1 = np.array([[[20, 0], [-4, 0]]], np.int16)
+    m = np.ones((1, 2), np.uint8)
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 2, 1, level=1), [[0, 1]])
+    np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 2, 1, level=0), [[1, 0]])
