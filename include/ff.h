@@ -163,6 +163,19 @@ ff_status ff_filter_2way(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *fl
 ff_status ff_region_filter(ff_ctx *ctx, const int16_t *flow_fwd, const uint8_t *mask_in,
                            int min_region, uint8_t *mask_out);
 
+/* Sec. 3.7-3.8 sparsification before dense interpolation.  The final grid
+ * is cut into q x q cells from its origin (border cells may be partial).  A
+ * cell holding at least e points of mask_in keeps exactly one in mask_out:
+ * the one whose consistency errors |F(p) + F_b(q)| (q as in ff_filter),
+ * summed over flow_bwd1 and flow_bwd2, are smallest (flow_bwd2 NULL: one
+ * backward flow).  Errors are IEEE double lengths in 1/8 px added in that
+ * order; an unset flow or q off the grid counts as infinite; ties go to the
+ * first point in raster order.  Other points get 0.  1 <= q <= 64, e >= 0.
+ * mask_in and mask_out may be the same buffer. */
+ff_status ff_sparsify(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_bwd1,
+                      const int16_t *flow_bwd2, const uint8_t *mask_in, int q, int e,
+                      uint8_t *mask_out);
+
 /* Whole pair with HOST buffers (blocking): copies both frames in (planar
  * uint8 [channels][h][w]), builds features, matches forward and backward
  * concurrently, filters (and region-filters when cfg.region_min > 0), and
@@ -234,8 +247,8 @@ ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
  * 0) stops.  ff_kernel_stats (call after ff_sync) returns, for the kernel
  * named `kernel` ("k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge",
  * "k_seed_rerank", "k_seed_given", "k_upsample", "k_sweep", "k_export",
- * "k_filter", "k_dense", "k_region"), the number of recorded launches and their summed
- * device time in milliseconds. */
+ * "k_filter", "k_dense", "k_region", "k_sparsify"), the number of recorded
+ * launches and their summed device time in milliseconds. */
 ff_status ff_profile(ff_ctx *ctx, int enable);
 ff_status ff_kernel_stats(ff_ctx *ctx, const char *kernel, long long *launches,
                           double *total_ms);

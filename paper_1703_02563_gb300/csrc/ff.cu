@@ -2,6 +2,7 @@
 // patch-matching loop (arXiv 1703.02563, Sec. 3).  The ABI is declared in
 // include/ff.h.
 #include <cuda_runtime.h>
+#include <math_constants.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -411,6 +412,50 @@ __global__ void k_rf_apply(const uint8_t *mask_in, int N, int s, const int *__re
     mask_out[i] = m;
 }
 
+// ---- sparsification (Sec. 3.7-3.8) -------------------------------------
+// consistency error |F(p) + F_b(q)| in 1/8 px, q the final-grid point nearest
+// to p + F(p); infinite when a flow is unset or q is off the grid
+__device__ __forceinline__ double sp_error(uint32_t f, const uint32_t *__restrict__ bwd, int x,
+                                           int y, int W, int H, int L) {
+    if (flow_x(f) == -32768 || flow_y(f) == -32768) return CUDART_INF;
+    const int half = 4 << L, sh = 3 + L;
+    const int qx = x + ((flow_x(f) + half) >> sh), qy = y + ((flow_y(f) + half) >> sh);
+    if (qx < 0 || qx >= W || qy < 0 || qy >= H) return CUDART_INF;
+    const uint32_t b = bwd[qy * W + qx];
+    if (flow_x(b) == -32768 || flow_y(b) == -32768) return CUDART_INF;
+    const long long dx = flow_x(f) + flow_x(b), dy = flow_y(f) + flow_y(b);
+    return sqrt((double)(dx * dx + dy * dy));
+}
+
+// one thread per q x q cell: keep the kept point of smallest summed error
+// (first in raster order on ties) if the cell holds at least e kept points
+__global__ void k_sparsify(const uint32_t *__restrict__ fwd, const uint32_t *__restrict__ b1,
+                           const uint32_t *__restrict__ b2, const uint8_t *mask_in, int W, int H,
+                           int L, int q, int e, int cells_x, int ncells, uint8_t *mask_out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int cy = (c / cells_x) * q, cx = (c % cells_x) * q;
+    const int y1 = min(cy + q, H), x1 = min(cx + q, W);
+    int count = 0, best = -1;
+    double best_err = 0.0;
+    for (int y = cy; y < y1; y++)
+        for (int x = cx; x < x1; x++) {
+            const int i = y * W + x;
+            if (!mask_in[i]) continue;
+            count++;
+            const uint32_t f = fwd[i];
+            double err = sp_error(f, b1, x, y, W, H, L);
+            if (b2) err = err + sp_error(f, b2, x, y, W, H, L);
+            if (best < 0 || err < best_err) {
+                best = i;
+                best_err = err;
+            }
+        }
+    if (count < e) best = -1;
+    for (int y = cy; y < y1; y++)
+        for (int x = cx; x < x1; x++) mask_out[y * W + x] = (y * W + x == best) ? 1 : 0;
+}
+
 // level state -> caller's flow / cost arrays
 __global__ void k_export(const uint32_t *__restrict__ flow, const int *__restrict__ cost, int N,
                          uint32_t *__restrict__ flow_out, int *__restrict__ cost_out) {
@@ -543,7 +588,8 @@ ff_status check_cuda(ff_ctx *ctx, cudaError_t e, const char *what) {
 
 const char *const kKernelNames[] = {"k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge",
                                     "k_seed_rerank", "k_seed_given", "k_upsample",
-                                    "k_sweep", "k_export", "k_filter", "k_dense", "k_region"};
+                                    "k_sweep", "k_export", "k_filter", "k_dense", "k_region",
+                                    "k_sparsify"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 int kernel_id(const char *name) {
@@ -1270,6 +1316,29 @@ ff_status ff_region_filter(ff_ctx *c, const int16_t *flow_fwd, const uint8_t *ma
     if (s) return s;
     DeviceGuard guard(c->device);
     return region_into(c, flow_fwd, mask_in, min_region, mask_out);
+}
+
+ff_status ff_sparsify(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd1,
+                      const int16_t *flow_bwd2, const uint8_t *mask_in, int q, int e,
+                      uint8_t *mask_out) {
+    if (!c) return FF_EINVAL;
+    if (!flow_fwd || !flow_bwd1 || !mask_in || !mask_out)
+        return fail(c, FF_EINVAL, "NULL argument");
+    if (((uintptr_t)flow_fwd & 3) || ((uintptr_t)flow_bwd1 & 3) || ((uintptr_t)flow_bwd2 & 3))
+        return fail(c, FF_EINVAL, "flows must be 4-byte aligned");
+    if (q < 1 || q > 64 || e < 0) return fail(c, FF_EINVAL, "q must be 1..64 and e >= 0");
+    ff_status s = check_pair(c);
+    if (s) return s;
+    DeviceGuard guard(c->device);
+    const int Lf = final_level(c->cfg);
+    int W, H;
+    level_dims(c->fw[0], c->fh[0], Lf, &W, &H);
+    const int cells_x = (W + q - 1) / q, ncells = cells_x * ((H + q - 1) / q);
+    prof_begin(c, "k_sparsify");
+    k_sparsify<<<(ncells + 127) / 128, 128, 0, c->stream>>>(
+        (const uint32_t *)flow_fwd, (const uint32_t *)flow_bwd1, (const uint32_t *)flow_bwd2,
+        mask_in, W, H, Lf, q, e, cells_x, ncells, mask_out);
+    return check_launch(c, "k_sparsify");
 }
 
 ff_status ff_pair_host(ff_ctx *c, const uint8_t *img1_host, const uint8_t *img2_host, int w,

@@ -22,7 +22,8 @@ FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS = 1, 2, 3
 INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
-            "ff_match_until", "ff_filter", "ff_filter_2way", "ff_region_filter", "ff_pair_host", "ff_get_features", "ff_seed_knn",
+            "ff_match_until", "ff_filter", "ff_filter_2way", "ff_region_filter", "ff_sparsify",
+            "ff_pair_host", "ff_get_features", "ff_seed_knn",
             "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
             "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy",
             "ff_batch_create", "ff_batch_run", "ff_batch_set_stream", "ff_batch_sync",
@@ -68,6 +69,7 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_filter.argtypes = [P, P, P, P]
         L.ff_filter_2way.argtypes = [P, P, P, P, P]
         L.ff_region_filter.argtypes = [P, P, P, i, P]
+        L.ff_sparsify.argtypes = [P, P, P, P, P, i, i, P]
         L.ff_pair_host.argtypes = [P, P, P, i, i, u32, P, P, P]
         L.ff_get_features.argtypes = [P, i, i, P]
         L.ff_seed_knn.argtypes = [P, i, P, P]
@@ -227,6 +229,12 @@ def ff_region_filter(ctx: int, flow_fwd, mask_in, min_region: int, mask_out) -> 
                                        _ptr(mask_out)))
 
 
+def ff_sparsify(ctx: int, flow_fwd, flow_bwd1, flow_bwd2, mask_in, q: int, e: int,
+                mask_out) -> None:
+    _check(ctx, lib().ff_sparsify(ctx, _ptr(flow_fwd), _ptr(flow_bwd1), _ptr(flow_bwd2),
+                                  _ptr(mask_in), q, e, _ptr(mask_out)))
+
+
 def ff_pair_host(ctx: int, img1_host, img2_host, w: int, h: int, pair_id: int,
                  flow_fwd_host=None, flow_bwd_host=None, mask_host=None) -> None:
     _check(ctx, lib().ff_pair_host(ctx, _ptr(img1_host), _ptr(img2_host), w, h, pair_id,
@@ -273,7 +281,8 @@ def ff_kernel_stats(ctx: int, kernel: str) -> tuple[int, float]:
 
 
 KERNELS = ("k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge", "k_seed_rerank", "k_seed_given",
-           "k_upsample", "k_sweep", "k_export", "k_filter", "k_dense", "k_region")
+           "k_upsample", "k_sweep", "k_export", "k_filter", "k_dense", "k_region",
+           "k_sparsify")
 
 
 def ff_launch_count(ctx: int) -> int:
@@ -366,6 +375,11 @@ class Context:
     def region_filter(self, flow_fwd, mask, min_region: int):
         out = self.torch.empty_like(mask)
         ff_region_filter(self.ctx, flow_fwd, mask, min_region, out)
+        return out
+
+    def sparsify(self, flow_fwd, flow_bwd1, flow_bwd2, mask, q: int, e: int):
+        out = self.torch.empty_like(mask)
+        ff_sparsify(self.ctx, flow_fwd, flow_bwd1, flow_bwd2, mask, q, e, out)
         return out
 
     def features_of(self, slot: int, level: int):

@@ -100,3 +100,34 @@ def test_pair_path_applies_the_region_filter(schedule):
     for o in outs:
         np.testing.assert_array_equal(_host(o["mask"]), ref)
     ff.ff_batch_destroy(b)
+
+
+@pytest.mark.parametrize("schedule", [ff.FF_SCHED_BASIC, ff.FF_SCHED_PLUS_FAST_X2])
+@pytest.mark.parametrize("W,H", [(53, 41), (1, 1), (300, 7)])
+def test_sparsify_bit_exact(schedule, W, H):
+    rng = np.random.default_rng(W + 17 * H + schedule)
+    cfg = ff.Config(channels=1, scales=2, iters=1, max_width=W, max_height=H, schedule=schedule,
+                    seed_stride=2 if schedule == ff.FF_SCHED_PLUS_FAST_X2 else 1)
+    ctx = ff.Context(cfg)
+    ctx.features(0, _dev(np.zeros((1, H, W), np.uint8)))
+    ctx.features(1, _dev(np.zeros((1, H, W), np.uint8)))
+    L = cfg.final_level()
+    WL, HL = O.level_dims(W, H, L)
+    fwd = rng.integers(-40, 40, (HL, WL, 2)).astype(np.int16)
+    b1 = (-fwd + rng.integers(-12, 13, (HL, WL, 2))).astype(np.int16)
+    b2 = (-fwd + rng.integers(-12, 13, (HL, WL, 2))).astype(np.int16)
+    fwd[rng.random((HL, WL)) < 0.05] = (-32768, -32768)
+    b2[rng.random((HL, WL)) < 0.05] = (-32768, -32768)
+    for mask in (O.filter_mask2(fwd, b1, b2, 24, level=L),
+                 (rng.random((HL, WL)) < 0.6).astype(np.uint8)):   # arbitrary: infinite errors
+        dm = _dev(mask)
+        for q, e in ((1, 1), (3, 0), (3, 2), (4, 5), (8, 3), (64, 1)):
+            for bb in (None, b2):
+                got = ctx.sparsify(_dev(fwd), _dev(b1), None if bb is None else _dev(bb), dm, q, e)
+                np.testing.assert_array_equal(_host(got), O.sparsify(fwd, b1, bb, mask, q, e, L),
+                                              err_msg=f"q {q} e {e} two-way {bb is not None}")
+        ff.ff_sparsify(ctx.ctx, _dev(fwd), _dev(b1), None, dm, 3, 2, dm)   # in place
+        np.testing.assert_array_equal(_host(dm), O.sparsify(fwd, b1, None, mask, 3, 2, L))
+    with pytest.raises(ff.FFError):
+        ctx.sparsify(_dev(fwd), _dev(b1), None, dm, 0, 1)
+    ctx.close()
