@@ -32,6 +32,7 @@
  */
 #ifndef FF_H
 #define FF_H
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -313,6 +314,59 @@ long long ff_batch_launch_count(const ff_batch *b);
 
 const char *ff_batch_last_error(const ff_batch *b);
 void ff_batch_destroy(ff_batch *b);
+
+/* ---- Serving loop ---------------------------------------------------------
+ * Continuous admission of frame-pair requests with HOST buffers.  Like the
+ * batched form it has no counterpart in the paper and changes nothing in
+ * what a pair computes.  A server owns as many slots as its device-memory
+ * budget holds (ff_slot_bytes each, at most max_slots); each slot keeps its
+ * pyramids, states and staging resident on the device.  A request goes into
+ * the first free slot as soon as there is one, so requests that arrive while
+ * others run overlap with them on the device; the rest wait in arrival
+ * order.  Calls are not thread-safe: one host thread drives a server. */
+typedef struct ff_server ff_server;
+
+typedef struct {
+    const uint8_t *img1;  /* host, planar uint8: channel k, row y, column x at        */
+    const uint8_t *img2;  /*   img[k * plane + y * pitch + x]; read until completion  */
+    int w, h, pitch;      /* 1 <= w <= max_width, 1 <= h <= max_height, pitch >= w     */
+    long long plane;      /* elements between channel planes, >= (h - 1) * pitch + w  */
+    uint32_t pair_id;     /* random-search key word 1                                  */
+    int two_way;          /* nonzero: second backward flow and two-way check          */
+    int16_t *flow_fwd;    /* host, final grid [..][..][2], or NULL                     */
+    int16_t *flow_bwd;    /* host or NULL                                              */
+    int16_t *flow_bwd2;   /* host or NULL (used when two_way)                          */
+    uint8_t *mask;        /* host, final grid, or NULL; region-filtered when           */
+                          /*   cfg.region_min > 0                                      */
+} ff_host_pair;
+
+/* Device bytes one slot (one context) of this config holds. */
+size_t ff_slot_bytes(const ff_config *cfg);
+
+/* Creates min(max_slots, mem_budget / ff_slot_bytes(cfg)) slots on `device`
+ * (FF_ENOMEM if not even one fits). */
+ff_status ff_server_create(const ff_config *cfg, int device, size_t mem_budget, int max_slots,
+                           ff_server **out);
+int ff_server_slots(const ff_server *srv);
+
+/* Queues a request (the descriptor is copied; the buffers it points to must
+ * live until the request completes), admits what fits and returns at once.
+ * *ticket (may be NULL) receives its number: 0, 1, 2, ... in submit order. */
+ff_status ff_server_submit(ff_server *srv, const ff_host_pair *req, long long *ticket);
+
+/* Retires finished requests without waiting: writes up to cap (ticket,
+ * status) pairs, *n_done of them (status FF_OK, FF_ETIMEOUT when a bounded
+ * device wait expired, FF_ECUDA), then admits queued requests into the
+ * freed slots.  A retired request's outputs are on the host. */
+ff_status ff_server_poll(ff_server *srv, long long *tickets, int *status, int cap, int *n_done);
+
+/* Requests submitted and not yet retired. */
+int ff_server_pending(const ff_server *srv);
+
+long long ff_server_launch_count(const ff_server *srv);
+const char *ff_server_last_error(const ff_server *srv);
+/* Waits for the device, then frees everything (unretired results are lost). */
+void ff_server_destroy(ff_server *srv);
 
 #ifdef __cplusplus
 }

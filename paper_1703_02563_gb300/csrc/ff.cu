@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <deque>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -545,7 +546,7 @@ struct ff_ctx {
     size_t edge_cap = 0;
     // staging for ff_pair_host
     uint8_t *img_dev[2] = {nullptr, nullptr};
-    uint32_t *pair_flow[2] = {nullptr, nullptr};
+    uint32_t *pair_flow[3] = {nullptr, nullptr, nullptr};   // fwd, bwd, second bwd
     uint8_t *pair_mask = nullptr;
     // region filter scratch: union-find parents, region sizes, join flags
     int *rf_parent = nullptr, *rf_size = nullptr;
@@ -666,6 +667,7 @@ void free_all(ff_ctx *c) {
         cudaFree(c->feat[s]);
         cudaFree(c->img_dev[s]);
         cudaFree(c->pair_flow[s]);
+        if (s == 1) cudaFree(c->pair_flow[2]);
     }
     for (int s = 0; s < kNumDirs; s++) {
         DirState &d = c->dir[s];
@@ -1189,6 +1191,7 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
         e = alloc(&c->feat[s], c->feat_cap);
         if (e == cudaSuccess) e = alloc(&c->img_dev[s], npix * c->C);
         if (e == cudaSuccess) e = alloc(&c->pair_flow[s], npix);
+        if (e == cudaSuccess && s == 1) e = alloc(&c->pair_flow[2], npix);
     }
     for (int s = 0; s < kNumDirs && e == cudaSuccess; s++) {
         DirState &d = c->dir[s];
@@ -1787,6 +1790,243 @@ void ff_batch_destroy(ff_batch *b) {
         batch_free(b);
     }
     delete b;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// serving loop
+// ============================================================================
+namespace {
+
+struct ServerSlot {
+    ff_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int *err_host = nullptr;        // pinned: the three error words after the pair
+    long long ticket = -1;          // -1: free
+};
+
+struct Pending {
+    ff_host_pair p;
+    long long ticket;
+};
+
+}  // namespace
+
+struct ff_server {
+    ff_config cfg;
+    int device = 0;
+    size_t slot_bytes = 0;
+    std::vector<ServerSlot> slot;
+    std::deque<Pending> queue;
+    long long next_ticket = 0;
+    long long launches = 0;
+    std::string last_error;
+};
+
+namespace {
+
+ff_status sfail(ff_server *v, ff_status s, const std::string &msg) {
+    v->last_error = msg;
+    return s;
+}
+
+// device bytes ff_create allocates for one context (and so one slot)
+size_t context_bytes(const ff_config &cfg) {
+    const int C = cfg.channels, P = C == 1 ? 16 : 32, K = C == 1 ? 16 : 32;
+    const size_t npix = (size_t)cfg.max_width * cfg.max_height;
+    int WS, HS;
+    level_dims(cfg.max_width, cfg.max_height, cfg.scales - 1, &WS, &HS);
+    const size_t nq = (size_t)WS * HS;
+    const int R = rows_per_strip(C, 1);
+    const size_t edge = (size_t)((cfg.max_height + R - 1) / R) * cfg.max_width;
+    size_t b = 2 * level_offset(cfg.max_width, cfg.max_height, P, cfg.scales);   // features
+    b += 2 * npix * C + 3 * npix * 4 + npix;                                    // staging
+    b += npix * (4 + 4 + 1);                                                    // region scratch
+    const size_t dir = npix * 4 * 4 + edge * 8 + FF_MAX_SCALES * kMaxIters * 4 +
+                       nq * FF_MAX_LEAF * 8 + nq * kMaxChunks * 8 * 8 + nq * K * 2 + nq * 4 +
+                       nq * kMaxChunks * 4 + npix * K * 2 + 4;
+    return b + kNumDirs * dir;
+}
+
+// enqueue one request on a free slot: frames in, the pair, results out,
+// error words out, completion event
+ff_status server_start(ff_server *v, ServerSlot &sl, const Pending &q) {
+    ff_ctx *c = sl.ctx;
+    const ff_host_pair &p = q.p;
+    const int C = c->C;
+    ff_status s;
+    for (int k = 0; k < C; k++) {
+        if ((s = check_cuda(c, cudaMemcpy2DAsync(c->img_dev[0] + (size_t)k * p.w * p.h, p.w,
+                                                 p.img1 + (size_t)k * p.plane, p.pitch, p.w, p.h,
+                                                 cudaMemcpyHostToDevice, sl.stream),
+                            "copy img1")))
+            return s;
+        if ((s = check_cuda(c, cudaMemcpy2DAsync(c->img_dev[1] + (size_t)k * p.w * p.h, p.w,
+                                                 p.img2 + (size_t)k * p.plane, p.pitch, p.w, p.h,
+                                                 cudaMemcpyHostToDevice, sl.stream),
+                            "copy img2")))
+            return s;
+    }
+    if ((s = enqueue_pair(c, c->img_dev[0], c->img_dev[1], p.w, p.h, p.w, p.pair_id,
+                          (int16_t *)c->pair_flow[0], (int16_t *)c->pair_flow[1],
+                          p.two_way ? (int16_t *)c->pair_flow[2] : nullptr, c->pair_mask)))
+        return s;
+    int WL, HL;
+    level_dims(p.w, p.h, final_level(c->cfg), &WL, &HL);
+    const size_t n = (size_t)WL * HL;
+    const struct {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } out[4] = {{p.flow_fwd, c->pair_flow[0], n * 4},
+                {p.flow_bwd, c->pair_flow[1], n * 4},
+                {p.two_way ? p.flow_bwd2 : nullptr, c->pair_flow[2], n * 4},
+                {p.mask, c->pair_mask, n}};
+    for (const auto &o : out)
+        if (o.dst && (s = check_cuda(c, cudaMemcpyAsync(o.dst, o.src, o.bytes,
+                                                        cudaMemcpyDeviceToHost, sl.stream),
+                                     "copy result")))
+            return s;
+    for (int d = 0; d < kNumDirs; d++)
+        if ((s = check_cuda(c, cudaMemcpyAsync(sl.err_host + d, c->dir[d].err, sizeof(int),
+                                               cudaMemcpyDeviceToHost, sl.stream),
+                            "copy error word")))
+            return s;
+    if ((s = check_cuda(c, cudaEventRecord(sl.done, sl.stream), "event"))) return s;
+    sl.ticket = q.ticket;
+    return FF_OK;
+}
+
+// move queued requests into free slots, in arrival order
+ff_status server_admit(ff_server *v) {
+    for (ServerSlot &sl : v->slot) {
+        if (v->queue.empty()) break;
+        if (sl.ticket >= 0) continue;
+        const long long l0 = sl.ctx->launches;
+        const ff_status s = server_start(v, sl, v->queue.front());
+        v->launches += sl.ctx->launches - l0;
+        if (s) return sfail(v, s, sl.ctx->last_error);
+        v->queue.pop_front();
+    }
+    return FF_OK;
+}
+
+void server_free(ff_server *v) {
+    for (ServerSlot &sl : v->slot) {
+        if (sl.ctx) ff_destroy(sl.ctx);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.err_host) cudaFreeHost(sl.err_host);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ff_slot_bytes(const ff_config *cfg) { return cfg ? context_bytes(*cfg) : 0; }
+
+ff_status ff_server_create(const ff_config *cfg, int device, size_t mem_budget, int max_slots,
+                           ff_server **out) {
+    if (!cfg || !out) return FF_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (validate_config(cfg, &why) != FF_OK || max_slots < 1 || max_slots > 1024)
+        return FF_EINVAL;
+    const size_t per = context_bytes(*cfg);
+    size_t nslots = mem_budget / per;
+    if (nslots < 1) return FF_ENOMEM;
+    if (nslots > (size_t)max_slots) nslots = (size_t)max_slots;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FF_ECUDA;
+    DeviceGuard guard(device);
+    ff_server *v = new ff_server();
+    v->cfg = *cfg;
+    v->device = device;
+    v->slot_bytes = per;
+    v->slot.resize(nslots);
+    ff_status s = FF_OK;
+    cudaError_t e = cudaSuccess;
+    for (ServerSlot &sl : v->slot) {
+        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.err_host, kNumDirs * sizeof(int));
+        if (e == cudaSuccess) s = ff_create(cfg, device, sl.stream, &sl.ctx);
+        if (e != cudaSuccess || s != FF_OK) break;
+    }
+    if (e != cudaSuccess || s != FF_OK) {
+        server_free(v);
+        delete v;
+        cudaGetLastError();
+        return s != FF_OK ? s : (e == cudaErrorMemoryAllocation ? FF_ENOMEM : FF_ECUDA);
+    }
+    *out = v;
+    return FF_OK;
+}
+
+int ff_server_slots(const ff_server *v) { return v ? (int)v->slot.size() : 0; }
+
+ff_status ff_server_submit(ff_server *v, const ff_host_pair *p, long long *ticket) {
+    if (!v) return FF_EINVAL;
+    if (!p || !p->img1 || !p->img2) return sfail(v, FF_EINVAL, "NULL request or image");
+    if (p->w < 1 || p->h < 1 || p->w > v->cfg.max_width || p->h > v->cfg.max_height)
+        return sfail(v, FF_EINVAL, "frame size exceeds max_width/max_height");
+    if (p->pitch < p->w || p->plane < (long long)(p->h - 1) * p->pitch + p->w)
+        return sfail(v, FF_EINVAL, "pitch < width or plane too small");
+    DeviceGuard guard(v->device);
+    const long long t = v->next_ticket++;
+    v->queue.push_back(Pending{*p, t});
+    if (ticket) *ticket = t;
+    return server_admit(v);
+}
+
+ff_status ff_server_poll(ff_server *v, long long *tickets, int *status, int cap, int *n_done) {
+    if (!v || !n_done || cap < 0 || (cap > 0 && (!tickets || !status))) return FF_EINVAL;
+    DeviceGuard guard(v->device);
+    *n_done = 0;
+    for (ServerSlot &sl : v->slot) {
+        if (sl.ticket < 0 || *n_done >= cap) continue;
+        const cudaError_t e = cudaEventQuery(sl.done);
+        if (e == cudaErrorNotReady) continue;
+        int st = FF_OK;
+        if (e != cudaSuccess) {
+            v->last_error = std::string("pair failed: ") + cudaGetErrorString(e);
+            st = FF_ECUDA;
+        } else if (sl.err_host[0] || sl.err_host[1] || sl.err_host[2]) {
+            for (int d = 0; d < kNumDirs; d++)
+                cudaMemsetAsync(sl.ctx->dir[d].err, 0, sizeof(int), sl.stream);
+            v->last_error = "a bounded device wait expired during matching";
+            st = FF_ETIMEOUT;
+        }
+        tickets[*n_done] = sl.ticket;
+        status[*n_done] = st;
+        (*n_done)++;
+        sl.ticket = -1;
+    }
+    return server_admit(v);
+}
+
+int ff_server_pending(const ff_server *v) {
+    if (!v) return 0;
+    int n = (int)v->queue.size();
+    for (const ServerSlot &sl : v->slot) n += sl.ticket >= 0;
+    return n;
+}
+
+long long ff_server_launch_count(const ff_server *v) { return v ? v->launches : 0; }
+
+const char *ff_server_last_error(const ff_server *v) { return v ? v->last_error.c_str() : ""; }
+
+void ff_server_destroy(ff_server *v) {
+    if (!v) return;
+    {
+        DeviceGuard guard(v->device);
+        cudaDeviceSynchronize();
+        server_free(v);
+    }
+    delete v;
 }
 
 }  // extern "C"

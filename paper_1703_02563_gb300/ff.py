@@ -27,7 +27,10 @@ EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "f
             "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
             "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy",
             "ff_batch_create", "ff_batch_run", "ff_batch_set_stream", "ff_batch_sync",
-            "ff_batch_launch_count", "ff_batch_last_error", "ff_batch_destroy")
+            "ff_batch_launch_count", "ff_batch_last_error", "ff_batch_destroy",
+            "ff_slot_bytes", "ff_server_create", "ff_server_slots", "ff_server_submit",
+            "ff_server_poll", "ff_server_pending", "ff_server_launch_count",
+            "ff_server_last_error", "ff_server_destroy")
 
 
 class ff_config(ct.Structure):
@@ -42,6 +45,13 @@ class ff_pair_desc(ct.Structure):
     _fields_ = [("img1", ct.c_void_p), ("img2", ct.c_void_p), ("w", ct.c_int), ("h", ct.c_int),
                 ("pitch", ct.c_int), ("pair_id", ct.c_uint32), ("flow_fwd", ct.c_void_p),
                 ("flow_bwd", ct.c_void_p), ("flow_bwd2", ct.c_void_p), ("mask", ct.c_void_p)]
+
+
+class ff_host_pair(ct.Structure):
+    _fields_ = [("img1", ct.c_void_p), ("img2", ct.c_void_p), ("w", ct.c_int), ("h", ct.c_int),
+                ("pitch", ct.c_int), ("plane", ct.c_longlong), ("pair_id", ct.c_uint32),
+                ("two_way", ct.c_int), ("flow_fwd", ct.c_void_p), ("flow_bwd", ct.c_void_p),
+                ("flow_bwd2", ct.c_void_p), ("mask", ct.c_void_p)]
 
 
 class FFError(RuntimeError):
@@ -98,10 +108,25 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_batch_last_error.restype = ct.c_char_p
         L.ff_batch_destroy.argtypes = [P]
         L.ff_batch_destroy.restype = None
+        L.ff_slot_bytes.argtypes = [ct.POINTER(ff_config)]
+        L.ff_slot_bytes.restype = ct.c_size_t
+        L.ff_server_create.argtypes = [ct.POINTER(ff_config), i, ct.c_size_t, i, ct.POINTER(P)]
+        L.ff_server_slots.argtypes = [P]
+        L.ff_server_submit.argtypes = [P, ct.POINTER(ff_host_pair), ct.POINTER(ct.c_longlong)]
+        L.ff_server_poll.argtypes = [P, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_int), i,
+                                     ct.POINTER(ct.c_int)]
+        L.ff_server_pending.argtypes = [P]
+        L.ff_server_launch_count.argtypes = [P]
+        L.ff_server_launch_count.restype = ct.c_longlong
+        L.ff_server_last_error.argtypes = [P]
+        L.ff_server_last_error.restype = ct.c_char_p
+        L.ff_server_destroy.argtypes = [P]
+        L.ff_server_destroy.restype = None
         for name in EXPORTED:
             if name not in ("ff_last_error", "ff_status_string", "ff_destroy",
                             "ff_launch_count", "ff_batch_launch_count", "ff_batch_last_error",
-                            "ff_batch_destroy"):
+                            "ff_batch_destroy", "ff_slot_bytes", "ff_server_launch_count",
+                            "ff_server_last_error", "ff_server_destroy"):
                 getattr(L, name).restype = ct.c_int
         _lib = L
     return _lib
@@ -452,3 +477,63 @@ def ff_batch_launch_count(b: int) -> int:
 
 def ff_batch_destroy(b: int) -> None:
     lib().ff_batch_destroy(b)
+
+
+# ---- serving loop ------------------------------------------------------------
+def _scheck(v, status: int):
+    if status != FF_OK:
+        msg = lib().ff_server_last_error(v).decode() if v else ""
+        raise FFError(status, msg)
+
+
+def ff_slot_bytes(cfg: Config) -> int:
+    c = cfg.c()
+    return int(lib().ff_slot_bytes(ct.byref(c)))
+
+
+def ff_server_create(cfg: Config, device: int = 0, mem_budget: int = 8 << 30,
+                     max_slots: int = 64) -> int:
+    out = ct.c_void_p()
+    c = cfg.c()
+    _scheck(None, lib().ff_server_create(ct.byref(c), device, mem_budget, max_slots,
+                                         ct.byref(out)))
+    return out.value
+
+
+def ff_server_slots(v: int) -> int:
+    return int(lib().ff_server_slots(v))
+
+
+def host_pair(img1, img2, w: int, h: int, pitch: int | None = None, plane: int | None = None,
+              pair_id: int = 0, two_way: bool = False, flow_fwd=None, flow_bwd=None,
+              flow_bwd2=None, mask=None) -> ff_host_pair:
+    pitch = w if pitch is None else pitch
+    plane = h * pitch if plane is None else plane
+    return ff_host_pair(_ptr(img1), _ptr(img2), w, h, pitch, plane, pair_id, int(two_way),
+                        _ptr(flow_fwd), _ptr(flow_bwd), _ptr(flow_bwd2), _ptr(mask))
+
+
+def ff_server_submit(v: int, req: ff_host_pair) -> int:
+    t = ct.c_longlong()
+    _scheck(v, lib().ff_server_submit(v, ct.byref(req), ct.byref(t)))
+    return t.value
+
+
+def ff_server_poll(v: int, cap: int = 256) -> list[tuple[int, int]]:
+    tickets = (ct.c_longlong * cap)()
+    status = (ct.c_int * cap)()
+    n = ct.c_int()
+    _scheck(v, lib().ff_server_poll(v, tickets, status, cap, ct.byref(n)))
+    return [(tickets[k], status[k]) for k in range(n.value)]
+
+
+def ff_server_pending(v: int) -> int:
+    return int(lib().ff_server_pending(v))
+
+
+def ff_server_launch_count(v: int) -> int:
+    return int(lib().ff_server_launch_count(v))
+
+
+def ff_server_destroy(v: int) -> None:
+    lib().ff_server_destroy(v)

@@ -534,3 +534,43 @@ def make_batch(n: int = 64, seed: int = 4, sizes=BATCH_SIZES, workers: int = 0,
         with mp.get_context("spawn").Pool(min(workers, n)) as pool:
             return pool.map(_batch_pair_args, args)
     return [batch_pair(*a) for a in args]
+
+
+# ----------------------------------------------------------------------------
+# serving workload: requests of sizes 256x256 .. 1920x1080 in 64-px steps
+# ----------------------------------------------------------------------------
+SERVE_WIDTHS = tuple(range(256, 1921, 64))
+SERVE_HEIGHTS = tuple(range(256, 1025, 64)) + (1080,)
+
+
+def _serving_base(seed: int) -> FramePair:
+    return layered_pair(seed=seed, width=1920, height=1080, channels=3, max_disp=300.0)
+
+
+def serving_bases(n: int = 4, seed: int = 6, workers: int = 0) -> list[FramePair]:
+    """n full-HD layered pairs (displacements up to 300 px) that requests are
+    cut from; `workers` > 1 generates them in a 'spawn' process pool."""
+    seeds = [seed * 1000 + k for k in range(n)]
+    if workers > 1 and n > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, n)) as pool:
+            return pool.map(_serving_base, seeds)
+    return [_serving_base(s) for s in seeds]
+
+
+def serving_requests(n: int, n_bases: int, seed: int = 7, widths=SERVE_WIDTHS,
+                     heights=SERVE_HEIGHTS, base_w: int = 1920,
+                     base_h: int = 1080) -> list[dict]:
+    """n requests: a size drawn uniformly from widths x heights, a base pair
+    (base_w x base_h) and a crop offset inside it; cropping both frames at
+    the same window keeps the pair's flow (the crop of the ground truth)."""
+    assert max(widths) <= base_w and max(heights) <= base_h
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        w = int(widths[int(rng.integers(0, len(widths)))])
+        h = int(heights[int(rng.integers(0, len(heights)))])
+        out.append(dict(base=int(rng.integers(0, n_bases)), w=w, h=h,
+                        x0=int(rng.integers(0, base_w - w + 1)),
+                        y0=int(rng.integers(0, base_h - h + 1)), pair_id=k))
+    return out

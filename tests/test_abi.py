@@ -61,3 +61,17 @@ def test_host_side_argument_checks_need_no_gpu():
     bad = ff.Config(max_width=5000).c()
     assert lib.ff_create(ct.byref(bad), 0, None, ct.byref(out)) == ff.FF_EINVAL
     lib.ff_destroy(None)
+
+
+def test_server_admission_by_memory_needs_no_gpu():
+    cfg = ff.Config(channels=3, scales=4, iters=6, max_width=1024, max_height=436)
+    per = ff.ff_slot_bytes(cfg)
+    # the features alone: 2 frames x 4 levels of 32-byte vectors
+    assert per > 2 * 1024 * 436 * 32
+    big = ff.Config(channels=3, scales=4, iters=6, max_width=1920, max_height=1080)
+    assert ff.ff_slot_bytes(big) > 4 * per
+    # a budget below one slot is refused before any device call
+    out = ct.c_void_p()
+    c = cfg.c()
+    assert ff.lib().ff_server_create(ct.byref(c), 0, per - 1, 8, ct.byref(out)) == ff.FF_ENOMEM
+    assert out.value is None
