@@ -95,6 +95,8 @@ typedef struct {
     int schedule;     /* an ff_schedule value                                             */
     int region_min;   /* s of the region filter (Sec. 3.7) applied after the consistency  */
                       /* check by ff_pair_host and ff_batch_run; 0 = off (default)        */
+    int wht_tensor_cores; /* 1: ff_features computes the WHT on the bf16 tensor cores     */
+                      /* (FP32 accumulation; exact, so the int8 features are identical)  */
 } ff_config;
 
 /* Fills the paper's defaults: patch 8, 9 coefficients, 1 channel, S = 4,
@@ -187,6 +189,16 @@ ff_status ff_sparsify(ff_ctx *ctx, const int16_t *flow_fwd, const int16_t *flow_
 ff_status ff_pair_host(ff_ctx *ctx, const uint8_t *img1_host, const uint8_t *img2_host,
                        int w, int h, uint32_t pair_id, int16_t *flow_fwd_host,
                        int16_t *flow_bwd_host, uint8_t *mask_host);
+
+/* The WHT of ff_features on the bf16 tensor cores, before quantisation:
+ * coeffs_out float [H_L][W_L][9 * channels] (dimension ch*9 + 3u + v) of
+ * level `level` of a device frame img (planar [channels][h][pitch]).  With
+ * 8-bit level images and +-1 bases every product and partial sum is an
+ * integer below 2^24, so the values are exact.  Stateless; enqueued on
+ * cuda_stream.  No paper counterpart: it exposes the intermediate for the
+ * precision check against an FP64 transform. */
+ff_status ff_wht_coeffs_tc(const uint8_t *img, int w, int h, int pitch, int channels, int level,
+                           float *coeffs_out, void *cuda_stream);
 
 /* Copies level `level` of slot `slot`'s features to dst: int8
  * [H_L][W_L][9 * channels] (dense, dimension index ch*9 + 3u + v). */

@@ -327,6 +327,7 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
 
 #include "ff_sweep.cuh"
 #include "ff_seed.cuh"
+#include "ff_wht_tc.cuh"
 
 // ---- region filter (Sec. 3.7) ------------------------------------------
 // Kept points are joined into regions by a lock-free union-find: a root only
@@ -711,6 +712,8 @@ ff_status validate_config(const ff_config *c, std::string *why) {
     if (c->eps_q3 < 0 || c->eps_q3 > 65535) return *why = "eps_q3 out of range", FF_EINVAL;
     if (c->schedule < FF_SCHED_BASIC || c->schedule > FF_SCHED_PLUS_FAST_X2)
         return *why = "unknown schedule", FF_EINVAL;
+    if (c->wht_tensor_cores != 0 && c->wht_tensor_cores != 1)
+        return *why = "wht_tensor_cores must be 0 or 1", FF_EINVAL;
     if (c->region_min < 0 || c->region_min > (1 << 24))
         return *why = "region_min out of range", FF_EINVAL;
     if (c->schedule == FF_SCHED_PLUS_FAST_X2 && c->scales < 2)
@@ -1255,10 +1258,18 @@ ff_status ff_features(ff_ctx *c, int slot, const uint8_t *img, int w, int h, int
         uint8_t *out = c->feat[slot] + level_offset(w, h, c->P, L);
         dim3 grid((WL + 15) / 16, (HL + 15) / 16), block(16, 16);
         prof_begin(c, "k_features");
-        if (c->C == 1)
+        if (c->cfg.wht_tensor_cores) {
+            if (c->C == 1)
+                k_features_tc<1, false><<<grid, 128, 0, c->stream>>>(img, pitch, w, h, L, WL, HL,
+                                                                     out, nullptr);
+            else
+                k_features_tc<3, false><<<grid, 128, 0, c->stream>>>(img, pitch, w, h, L, WL, HL,
+                                                                     out, nullptr);
+        } else if (c->C == 1) {
             k_features<1><<<grid, block, 0, c->stream>>>(img, pitch, w, h, L, WL, HL, out);
-        else
+        } else {
             k_features<3><<<grid, block, 0, c->stream>>>(img, pitch, w, h, L, WL, HL, out);
+        }
         ff_status s = check_launch(c, "k_features");
         if (s) return s;
     }
@@ -1319,6 +1330,24 @@ ff_status ff_region_filter(ff_ctx *c, const int16_t *flow_fwd, const uint8_t *ma
     if (s) return s;
     DeviceGuard guard(c->device);
     return region_into(c, flow_fwd, mask_in, min_region, mask_out);
+}
+
+ff_status ff_wht_coeffs_tc(const uint8_t *img, int w, int h, int pitch, int channels, int level,
+                           float *coeffs_out, void *cuda_stream) {
+    if (!img || !coeffs_out) return FF_EINVAL;
+    if (w < 1 || h < 1 || w > FF_MAX_DIM || h > FF_MAX_DIM || pitch < w) return FF_EINVAL;
+    if ((channels != 1 && channels != 3) || level < 0 || level >= FF_MAX_SCALES) return FF_EINVAL;
+    int WL, HL;
+    level_dims(w, h, level, &WL, &HL);
+    dim3 grid((WL + 15) / 16, (HL + 15) / 16);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (channels == 1)
+        k_features_tc<1, true><<<grid, 128, 0, st>>>(img, pitch, w, h, level, WL, HL, nullptr,
+                                                     coeffs_out);
+    else
+        k_features_tc<3, true><<<grid, 128, 0, st>>>(img, pitch, w, h, level, WL, HL, nullptr,
+                                                     coeffs_out);
+    return cudaGetLastError() == cudaSuccess ? FF_OK : FF_ECUDA;
 }
 
 ff_status ff_sparsify(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd1,

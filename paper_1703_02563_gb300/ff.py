@@ -22,7 +22,7 @@ FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS = 1, 2, 3
 INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
-            "ff_match_until", "ff_filter", "ff_filter_2way", "ff_region_filter", "ff_sparsify",
+            "ff_match_until", "ff_filter", "ff_filter_2way", "ff_region_filter", "ff_sparsify", "ff_wht_coeffs_tc",
             "ff_pair_host", "ff_get_features", "ff_seed_knn",
             "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
             "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy",
@@ -38,7 +38,8 @@ class ff_config(ct.Structure):
                 ("scales", ct.c_int), ("iters", ct.c_int), ("radius_q3", ct.c_int),
                 ("seed_leaf", ct.c_int), ("seed_stride", ct.c_int), ("eps_q3", ct.c_int),
                 ("seed", ct.c_uint32), ("max_width", ct.c_int), ("max_height", ct.c_int),
-                ("schedule", ct.c_int), ("region_min", ct.c_int)]
+                ("schedule", ct.c_int), ("region_min", ct.c_int),
+                ("wht_tensor_cores", ct.c_int)]
 
 
 class ff_pair_desc(ct.Structure):
@@ -80,6 +81,7 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_filter_2way.argtypes = [P, P, P, P, P]
         L.ff_region_filter.argtypes = [P, P, P, i, P]
         L.ff_sparsify.argtypes = [P, P, P, P, P, i, i, P]
+        L.ff_wht_coeffs_tc.argtypes = [P, i, i, i, i, i, P, P]
         L.ff_pair_host.argtypes = [P, P, P, i, i, u32, P, P, P]
         L.ff_get_features.argtypes = [P, i, i, P]
         L.ff_seed_knn.argtypes = [P, i, P, P]
@@ -173,6 +175,7 @@ class Config:
     n_coeffs: int = 9
     schedule: int = FF_SCHED_BASIC
     region_min: int = 0
+    wht_tensor_cores: int = 0
 
     def final_level(self) -> int:
         """The grid the schedule's matches come on (1 for Fast x2, else 0)."""
@@ -258,6 +261,12 @@ def ff_sparsify(ctx: int, flow_fwd, flow_bwd1, flow_bwd2, mask_in, q: int, e: in
                 mask_out) -> None:
     _check(ctx, lib().ff_sparsify(ctx, _ptr(flow_fwd), _ptr(flow_bwd1), _ptr(flow_bwd2),
                                   _ptr(mask_in), q, e, _ptr(mask_out)))
+
+
+def ff_wht_coeffs_tc(img, w: int, h: int, pitch: int, channels: int, level: int, coeffs_out,
+                     stream=None) -> None:
+    _check(None, lib().ff_wht_coeffs_tc(_ptr(img), w, h, pitch, channels, level,
+                                        _ptr(coeffs_out), _stream_handle(stream)))
 
 
 def ff_pair_host(ctx: int, img1_host, img2_host, w: int, h: int, pair_id: int,
