@@ -224,7 +224,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     schedule = SCHEDULES[args.schedule]
     cfg = ff.Config(channels=C, scales=S, iters=I, radius_q3=R, max_width=W, max_height=H,
                     schedule=schedule, seed_stride=2 if args.schedule == "fast_x2" else 1,
-                    region_min=args.region)
+                    region_min=args.region, wht_tensor_cores=int(args.wht_tc))
     WL, HL = level_dims(W, H, cfg.final_level())
     main = torch.cuda.Stream(dev)
     side = torch.cuda.Stream(dev)
@@ -510,6 +510,8 @@ def main():
                     help="second backward flow and two-way check (Sec. 3.7)")
     ap.add_argument("--region", type=int, default=0,
                     help="region filter s (Sec. 3.7) after the consistency check; 0 = off")
+    ap.add_argument("--wht-tc", action="store_true",
+                    help="features on the bf16 tensor cores (the precision form)")
     ap.add_argument("--serve", action="store_true",
                     help="run the serving loop on a Poisson request stream instead")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -626,6 +628,7 @@ def main():
                    "iters": I, "radius_q3": res["prm"]["radius_q3"], "seed_leaf": 8,
                    "schedule": args.schedule, "seed_stride": res["cfg"].seed_stride,
                    "backward_flows": n_dirs - 1, "region_min": args.region,
+                   "wht": "bf16 tensor cores, FP32 accumulation" if args.wht_tc else "int32 ALU",
                    "l2": "flushed between steps (256 MiB write outside the step events)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "clocks": res["clocks"],
