@@ -232,6 +232,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     ctx = ff.ff_create(cfg, local_rank, main)
     if args.sweep_warps:
         ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WARPS, args.sweep_warps)
+    if args.sweep_wpl:
+        ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WPL, args.sweep_wpl)
     img1 = torch.from_numpy(pair.img1).to(dev)
     img2 = torch.from_numpy(pair.img2).to(dev)
     flow_f = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
@@ -347,7 +349,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
 ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock (Tops/s)
 
 
-def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int) -> dict:
+def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int,
+                sweep_wpl: int = 0) -> dict:
     """Throughput of the batched form on `pairs` (inputs resident, L2
     flushed between steps, one graph launch per step timed with CUDA events
     on the batch's stream)."""
@@ -362,6 +365,8 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
                     radius_q3=prm["radius_q3"], max_width=W, max_height=H)
     stream = torch.cuda.Stream(dev)
     b = ff.ff_batch_create(cfg, local_rank, slots=slots, stream=stream)
+    if sweep_wpl:
+        ff.ff_batch_debug_set(b, ff.FF_DEBUG_SWEEP_WPL, sweep_wpl)
     imgs = [(torch.from_numpy(p.img1).to(dev), torch.from_numpy(p.img2).to(dev)) for p in pairs]
     outs = [tuple(torch.empty(s, dtype=t, device=dev)
                   for s, t in (((p.height, p.width, 2), torch.int16),
@@ -522,6 +527,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--sweep-warps", type=int, default=0,
                     help="propagation warps per sweep CTA (1, 2, 4; 0 = library default)")
+    ap.add_argument("--sweep-wpl", type=int, default=0,
+                    help="feature words per lane in the sweep (1, 2, 4; 0 = library default)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -599,7 +606,8 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world, local_rank)
-    batched = {name: run_batched(pairs, prm, args.batch_slots, args.batch_steps, 3, local_rank)
+    batched = {name: run_batched(pairs, prm, args.batch_slots, args.batch_steps, 3, local_rank,
+                                 args.sweep_wpl)
                for name, (pairs, prm) in batches.items()}
     total_s = res["total_ms"] / 1e3
     e2e_s = res["e2e_s"]

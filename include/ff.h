@@ -246,11 +246,14 @@ ff_status ff_sync(ff_ctx *ctx);
  * next propagation sweeps wait for a boundary row that is never written, so
  * the bounded wait runs out and ff_sync reports FF_ETIMEOUT.
  * FF_DEBUG_SWEEP_WARPS: propagation warps per sweep CTA (1, 2 or 4; default
- * 1); every value gives the same results. */
+ * 1).  FF_DEBUG_SWEEP_WPL: feature words (4 dimensions each) per lane in the
+ * sweep, 1, 2 or 4 (default 1 for gray, 2 for Lab); other than 2, one
+ * propagation warp per CTA.  Every value gives the same results. */
 typedef enum {
     FF_DEBUG_WAIT_LIMIT_NS = 1,
     FF_DEBUG_FORCE_TIMEOUT = 2,
-    FF_DEBUG_SWEEP_WARPS = 3
+    FF_DEBUG_SWEEP_WARPS = 3,
+    FF_DEBUG_SWEEP_WPL = 4
 } ff_debug_key;
 ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
 
@@ -320,6 +323,9 @@ ff_status ff_batch_set_stream(ff_batch *b, void *cuda_stream);
 /* Waits for the device and reports FF_ETIMEOUT if a bounded wait of any
  * slot expired (the words are cleared). */
 ff_status ff_batch_sync(ff_batch *b);
+
+/* ff_debug_set on every slot (a captured graph is dropped). */
+ff_status ff_batch_debug_set(ff_batch *b, ff_debug_key key, long long value);
 
 /* Kernel launches made by this batch so far (graph relaunches included). */
 long long ff_batch_launch_count(const ff_batch *b);

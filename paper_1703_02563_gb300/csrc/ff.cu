@@ -554,6 +554,7 @@ struct ff_ctx {
     uint8_t *rf_flag = nullptr;
     unsigned long long wait_ns = 2000000000ull;
     int sweep_warps = 1;   // propagation warps per sweep CTA: 1, 2 or 4
+    int sweep_wpl = 2;     // feature words per lane in the sweep: 1, 2 or 4 (set by ff_create)
     int force_timeout = 0;
     long long launches = 0;
     std::string last_error;
@@ -653,8 +654,13 @@ size_t level_offset(int W, int H, int P, int L) {
 }
 
 // rows per strip of the sweep kernel for `np` propagation warps per CTA
-int rows_per_strip(int C, int np) {
-    const int rw = C == 1 ? SweepGeo<1, 1>::RW : SweepGeo<3, 1>::RW;
+// rows of one sweep strip for np propagation warps and wpl feature words
+// per lane; wpl = 1 gives the smallest strips
+int rows_per_strip(int C, int np, int wpl) {
+    int rw;
+    if (wpl == 1) rw = C == 1 ? SweepGeo<1, 1, 1>::RW : SweepGeo<3, 1, 1>::RW;
+    else if (wpl == 4) rw = C == 1 ? SweepGeo<1, 1, 4>::RW : SweepGeo<3, 1, 4>::RW;
+    else rw = C == 1 ? SweepGeo<1, 1, 2>::RW : SweepGeo<3, 1, 2>::RW;
     return rw * np;
 }
 
@@ -873,19 +879,27 @@ ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L,
     a.epoch = 1u + (uint32_t)(L * kMaxIters + t);
     a.wait_ns = c->wait_ns;
     a.force_timeout = c->force_timeout;
-    const int R = rows_per_strip(c->C, c->sweep_warps);
+    const int R = rows_per_strip(c->C, c->sweep_warps, c->sweep_wpl);
     const int nstrips = (HL + R - 1) / R;
     prof_begin(c, "k_sweep");
-#define FF_LAUNCH_SWEEP(CC, NPW) \
-    k_sweep<CC, NPW><<<nstrips, SweepGeo<CC, NPW>::THREADS, 0, c->stream>>>(a)
-    if (c->C == 1) {
-        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(1, 1);
-        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(1, 2);
-        else FF_LAUNCH_SWEEP(1, 4);
+#define FF_LAUNCH_SWEEP(CC, NPW, WPL) \
+    k_sweep<CC, NPW, WPL><<<nstrips, SweepGeo<CC, NPW, WPL>::THREADS, 0, c->stream>>>(a)
+    if (c->sweep_wpl != 2) {   // one propagation warp per strip
+        if (c->C == 1) {
+            if (c->sweep_wpl == 1) FF_LAUNCH_SWEEP(1, 1, 1);
+            else FF_LAUNCH_SWEEP(1, 1, 4);
+        } else {
+            if (c->sweep_wpl == 1) FF_LAUNCH_SWEEP(3, 1, 1);
+            else FF_LAUNCH_SWEEP(3, 1, 4);
+        }
+    } else if (c->C == 1) {
+        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(1, 1, 2);
+        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(1, 2, 2);
+        else FF_LAUNCH_SWEEP(1, 4, 2);
     } else {
-        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(3, 1);
-        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(3, 2);
-        else FF_LAUNCH_SWEEP(3, 4);
+        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(3, 1, 2);
+        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(3, 2, 2);
+        else FF_LAUNCH_SWEEP(3, 4, 2);
     }
 #undef FF_LAUNCH_SWEEP
     return check_launch(c, "k_sweep");
@@ -1178,6 +1192,9 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     c->stream = (cudaStream_t)cuda_stream;
     c->C = cfg->channels;
     c->P = cfg->channels == 1 ? 16 : 32;
+    // measured fastest per pair on GB300: 4 lanes of one word per gray point,
+    // 4 lanes of two words per Lab point
+    c->sweep_wpl = cfg->channels == 1 ? 1 : 2;
     c->S = cfg->scales;
     c->I = cfg->iters;
     c->maxW = cfg->max_width;
@@ -1187,7 +1204,7 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     level_dims(c->maxW, c->maxH, c->S - 1, &WS, &HS);
     c->nq_cap = (size_t)WS * HS;
     const size_t npix = (size_t)c->maxW * c->maxH;
-    const int R = rows_per_strip(c->C, 1);   // the smallest strip
+    const int R = rows_per_strip(c->C, 1, 1);   // the smallest strip
     c->edge_cap = (size_t)((c->maxH + R - 1) / R) * c->maxW;
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < 2 && e == cudaSuccess; s++) {
@@ -1534,6 +1551,11 @@ ff_status ff_debug_set(ff_ctx *c, ff_debug_key key, long long value) {
                 return fail(c, FF_EINVAL, "sweep warps must be 1, 2 or 4");
             c->sweep_warps = (int)value;
             return FF_OK;
+        case FF_DEBUG_SWEEP_WPL:
+            if (value != 1 && value != 2 && value != 4)
+                return fail(c, FF_EINVAL, "sweep words per lane must be 1, 2 or 4");
+            c->sweep_wpl = (int)value;
+            return FF_OK;
     }
     return fail(c, FF_EINVAL, "unknown debug key");
 }
@@ -1807,6 +1829,20 @@ ff_status ff_batch_sync(ff_batch *b) {
     return FF_OK;
 }
 
+ff_status ff_batch_debug_set(ff_batch *b, ff_debug_key key, long long value) {
+    if (!b) return FF_EINVAL;
+    for (ff_ctx *c : b->slot) {
+        const ff_status s = ff_debug_set(c, key, value);
+        if (s) return bfail(b, s, c->last_error);
+    }
+    if (b->exec) {   // the captured graph holds the old launches
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        b->exec_desc.clear();
+    }
+    return FF_OK;
+}
+
 long long ff_batch_launch_count(const ff_batch *b) { return b ? b->launches : 0; }
 
 const char *ff_batch_last_error(const ff_batch *b) { return b ? b->last_error.c_str() : ""; }
@@ -1868,7 +1904,7 @@ size_t context_bytes(const ff_config &cfg) {
     int WS, HS;
     level_dims(cfg.max_width, cfg.max_height, cfg.scales - 1, &WS, &HS);
     const size_t nq = (size_t)WS * HS;
-    const int R = rows_per_strip(C, 1);
+    const int R = rows_per_strip(C, 1, 1);
     const size_t edge = (size_t)((cfg.max_height + R - 1) / R) * cfg.max_width;
     size_t b = 2 * level_offset(cfg.max_width, cfg.max_height, P, cfg.scales);   // features
     b += 2 * npix * C + 3 * npix * 4 + npix;                                    // staging

@@ -20,12 +20,14 @@ struct SweepArgs {
     int force_timeout;
 };
 
-// Lane layout: G lanes per grid point, two 4-dimension feature words (8
-// bytes) per lane; RW = 32/G rows per warp; NP propagation warps per strip,
-// each paired with a helper warp; one loader warp.
-template <int C, int NP_> struct SweepGeo {
+// Lane layout: G lanes per grid point, WPL 4-dimension feature words per
+// lane; RW = 32/G rows per warp; NP propagation warps per strip, each paired
+// with a helper warp; one loader warp.
+template <int C, int NP_, int WPL_ = 2> struct SweepGeo {
     static constexpr int P = Geo<C>::P;
-    static constexpr int G = P / 8;      // 2 (gray) or 4 (Lab) lanes per point
+    static constexpr int WPL = WPL_;     // feature words per lane: 1, 2 or 4
+    static constexpr int G = P / (4 * WPL);   // lanes per point
+    static_assert(G >= 1 && G <= 32 && G * 4 * WPL == P, "lane layout");
     static constexpr int RW = 32 / G;    // rows per warp
     static constexpr int NP = NP_;       // propagation warps (and as many helpers)
     static constexpr int R = NP * RW;    // rows per strip
@@ -37,15 +39,25 @@ template <int C, int NP_> struct SweepGeo {
     static constexpr int NB = 8 / G;     // random-search offsets per lane per 8 steps
     static constexpr int PD = 1;         // L1 warming distance (level pixels)
     static constexpr int PF_COLS = 4;    // feature columns warmed from the target on
-    static constexpr int PF_ROWS = G < 4 ? G : 4;   // feature rows warmed around the target
+    static constexpr int PF_ROWS = 4;    // feature rows warmed around the target
     static constexpr int THREADS = (2 * NP + 1) * 32;
 };
 
-template <int C, int NP> struct SweepShared {
-    using SG = SweepGeo<C, NP>;
+template <int WPL> struct QWords {
+    uint32_t w[WPL];
+};
+template <> struct __align__(8) QWords<2> {
+    uint32_t w[2];
+};
+template <> struct __align__(16) QWords<4> {
+    uint32_t w[4];
+};
+
+template <int C, int NP, int WPL> struct SweepShared {
+    using SG = SweepGeo<C, NP, WPL>;
     uint32_t in_flow[NP][SG::DI][SG::RW];
     int in_cost[NP][SG::DI][SG::RW];
-    uint2 in_q[NP][SG::DI][32];
+    QWords<WPL> in_q[NP][SG::DI][32];
     unsigned long long out[NP][SG::DO][SG::RW];   // (tag:12 | cost:20) << 32 | flow
     unsigned long long ring[NP][SG::RING];        // (column + 1) << 32 | flow
     unsigned long long lring[SG::LRING];          // (column + 1) << 32 | flow
@@ -57,6 +69,10 @@ template <int C, int NP> struct SweepShared {
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16ca(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -99,22 +115,78 @@ __device__ __forceinline__ Tap tap_at(int tx, int ty, int L, int WL, int HL) {
     return t;
 }
 
-// the 4 taps of one lane's two words (dimensions 8g .. 8g+7)
-struct Taps2 {
-    uint2 t00, t10, t01, t11;
-};
-__device__ __forceinline__ Taps2 load_taps(const uint8_t *f2L, const Tap &t, int g) {
-    const uint8_t *b = f2L + 8 * g;
-    Taps2 r;
-    r.t00 = ldg64(b + t.o00);
-    r.t10 = ldg64(b + t.o10);
-    r.t01 = ldg64(b + t.o01);
-    r.t11 = ldg64(b + t.o11);
+// WPL words of one feature vector (dimensions 4 WPL g .. 4 WPL g + 4 WPL - 1)
+template <int WPL>
+__device__ __forceinline__ QWords<WPL> ldg_words(const uint8_t *p) {
+    QWords<WPL> r;
+    if constexpr (WPL == 4) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        r.w[0] = v.x, r.w[1] = v.y, r.w[2] = v.z, r.w[3] = v.w;
+    } else if constexpr (WPL == 2) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        r.w[0] = v.x, r.w[1] = v.y;
+    } else {
+        r.w[0] = __ldg(reinterpret_cast<const unsigned int *>(p));
+    }
     return r;
 }
-__device__ __forceinline__ int sad2(const Taps2 &x, uint32_t w, int4 na0, int4 na1) {
-    return sad_word(x.t00.x, x.t10.x, x.t01.x, x.t11.x, w, na0) +
-           sad_word(x.t00.y, x.t10.y, x.t01.y, x.t11.y, w, na1);
+// the same words staged in shared memory (written by cp.async, read volatile)
+template <int WPL>
+__device__ __forceinline__ QWords<WPL> lds_words(const QWords<WPL> *p) {
+    QWords<WPL> r;
+    if constexpr (WPL == 4) {
+        uint32_t x, y, z, w;
+        asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(x), "=r"(y), "=r"(z), "=r"(w)
+                     : "r"((unsigned)__cvta_generic_to_shared(p)));
+        r.w[0] = x, r.w[1] = y, r.w[2] = z, r.w[3] = w;
+    } else if constexpr (WPL == 2) {
+        const unsigned long long v = *(const volatile unsigned long long *)p;
+        r.w[0] = (uint32_t)v, r.w[1] = (uint32_t)(v >> 32);
+    } else {
+        r.w[0] = *(const volatile uint32_t *)p;
+    }
+    return r;
+}
+template <int WPL>
+__device__ __forceinline__ void cp_async_words(QWords<WPL> *smem, const uint8_t *gmem) {
+    if constexpr (WPL == 4) cp_async16ca(smem, gmem);
+    else if constexpr (WPL == 2) cp_async8(smem, gmem);
+    else cp_async4(smem, gmem);
+}
+
+// the 4 taps of one lane's WPL words
+template <int WPL> struct Taps {
+    QWords<WPL> t00, t10, t01, t11;
+};
+template <int WPL>
+__device__ __forceinline__ Taps<WPL> load_taps(const uint8_t *f2L, const Tap &t, int g) {
+    const uint8_t *b = f2L + 4 * WPL * g;
+    Taps<WPL> r;
+    r.t00 = ldg_words<WPL>(b + t.o00);
+    r.t10 = ldg_words<WPL>(b + t.o10);
+    r.t01 = ldg_words<WPL>(b + t.o01);
+    r.t11 = ldg_words<WPL>(b + t.o11);
+    return r;
+}
+// -64 x the query words, the seeds of the interpolation dot products
+template <int WPL> struct NegQ {
+    int4 na[WPL];
+};
+template <int WPL>
+__device__ __forceinline__ NegQ<WPL> neg_query(const QWords<WPL> &q) {
+    NegQ<WPL> r;
+#pragma unroll
+    for (int j = 0; j < WPL; j++) r.na[j] = neg64(q.w[j]);
+    return r;
+}
+template <int WPL>
+__device__ __forceinline__ int sad_words(const Taps<WPL> &x, uint32_t w, const NegQ<WPL> &nq) {
+    int e = 0;
+#pragma unroll
+    for (int j = 0; j < WPL; j++)
+        e += sad_word(x.t00.w[j], x.t10.w[j], x.t01.w[j], x.t11.w[j], w, nq.na[j]);
+    return e;
 }
 
 // target (1/8 px) of flow f at grid point (px, py), clamped into the frame
@@ -179,14 +251,15 @@ __device__ __forceinline__ bool wait_expired(unsigned long long &t0, unsigned lo
 // Every wait is bounded and warp-uniform: a warp that sees no progress for
 // wait_ns sets the error word to FF_ETIMEOUT, raises the CTA's abort flag and
 // returns; every other wait in the CTA checks that flag on its slow path.
-template <int C, int NP>
-__global__ void __launch_bounds__(SweepGeo<C, NP>::THREADS) k_sweep(const SweepArgs a) {
-    using SG = SweepGeo<C, NP>;
+template <int C, int NP, int WPL>
+__global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const SweepArgs a) {
+    using SG = SweepGeo<C, NP, WPL>;
     constexpr int P = SG::P, G = SG::G, RW = SG::RW, R = SG::R;
     constexpr int DI = SG::DI, DO = SG::DO, A = SG::A, RING = SG::RING, LRING = SG::LRING;
-    constexpr int NB = SG::NB, PD = SG::PD, PF_ROWS = SG::PF_ROWS, PF_COLS = SG::PF_COLS;
+    constexpr int NB = SG::NB, PD = SG::PD, PF_ROWS = SG::PF_ROWS;
+    constexpr int PF_COLS = SG::PF_COLS;
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ SweepShared<C, NP> sm;
+    __shared__ SweepShared<C, NP, WPL> sm;
     volatile int *v_in_ready = sm.in_ready;
     volatile int *v_out_cons = sm.out_cons;
     volatile int *v_cons = sm.cons;
@@ -282,7 +355,7 @@ __global__ void __launch_bounds__(SweepGeo<C, NP>::THREADS) k_sweep(const SweepA
                 const int slot = j & (DI - 1);
                 if (g == 0) cp_async4(&sm.in_flow[w][slot][k], a.flow + pi);
                 if (g == G - 1) cp_async4(&sm.in_cost[w][slot][k], a.cost + pi);
-                cp_async8(&sm.in_q[w][slot][lane], f1L + pi * P + 8 * g);
+                cp_async_words<WPL>(&sm.in_q[w][slot][lane], f1L + pi * P + 4 * WPL * g);
             }
         };
         for (int j = 0; j < A; j++) {
@@ -332,7 +405,7 @@ __global__ void __launch_bounds__(SweepGeo<C, NP>::THREADS) k_sweep(const SweepA
                     return;
                 }
             }
-            const uint2 q = sm.in_q[w][i & (DI - 1)][lane];
+            const QWords<WPL> q = lds_words<WPL>(&sm.in_q[w][i & (DI - 1)][lane]);
             __syncwarp();
             if (lane == 0) v_out_cons[w] = i + 1;
             const uint32_t best = (uint32_t)e;
@@ -358,7 +431,7 @@ __global__ void __launch_bounds__(SweepGeo<C, NP>::THREADS) k_sweep(const SweepA
                 int er = 0;
                 if (__any_sync(FULL, nR)) {
                     const Tap tR = tap_at<P>(rtx, rty, L, U, V);
-                    er = sad2(load_taps(f2L, tR, g), tR.w, neg64(q.x), neg64(q.y));
+                    er = sad_words<WPL>(load_taps<WPL>(f2L, tR, g), tR.w, neg_query<WPL>(q));
                 }
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) er += __shfl_xor_sync(FULL, er, o);
@@ -404,11 +477,17 @@ __global__ void __launch_bounds__(SweepGeo<C, NP>::THREADS) k_sweep(const SweepA
             target_of(last, px + sxdir * PD * n, py, W, H, tx, ty);
             const int half = n >> 1;
             const int ix = min((tx + half) >> (L + 3), U - 1);
-            const int iy = clampi(((ty + half) >> (L + 3)) + g - (PF_ROWS > 2 ? 1 : 0), 0, V - 1);
-            const uint8_t *rowp = f2L + (size_t)iy * U * P;
+            const int iy0 = ((ty + half) >> (L + 3)) - 1;
 #pragma unroll
-            for (int cc = 0; cc < PF_COLS; cc++)
-                cp_async4(&sm.pf_sink[w][lane], rowp + (size_t)min(ix + cc, U - 1) * P);
+            for (int rr = 0; rr < (PF_ROWS + G - 1) / G; rr++) {
+                const int row = g + rr * G;
+                if (row < PF_ROWS) {
+                    const uint8_t *rowp = f2L + (size_t)clampi(iy0 + row, 0, V - 1) * U * P;
+#pragma unroll
+                    for (int cc = 0; cc < PF_COLS; cc++)
+                        cp_async4(&sm.pf_sink[w][lane], rowp + (size_t)min(ix + cc, U - 1) * P);
+                }
+            }
         }
         // staged inputs of step i, and (group 0) the vertical source of column i
         const bool need_top = top_src && i < U && k == 0;
@@ -441,9 +520,7 @@ __global__ void __launch_bounds__(SweepGeo<C, NP>::THREADS) k_sweep(const SweepA
             cur = ((volatile uint32_t *)sm.in_flow[w][islot])[k];
             ccost = ((volatile int *)sm.in_cost[w][islot])[k];
         }
-        const unsigned long long q64 =
-            lds64(reinterpret_cast<const unsigned long long *>(&sm.in_q[w][islot][lane]));
-        const uint2 q = make_uint2((uint32_t)q64, (uint32_t)(q64 >> 32));
+        const QWords<WPL> q = lds_words<WPL>(&sm.in_q[w][islot][lane]);
         const uint32_t hflow = (active && u > 0) ? last : kFlowInvalid;
         const bool vv = vflow != kFlowInvalid, hv = hflow != kFlowInvalid;
         int vtx, vty, htx, hty;
@@ -456,10 +533,10 @@ __global__ void __launch_bounds__(SweepGeo<C, NP>::THREADS) k_sweep(const SweepA
         int ev = 0, eh = 0;
         if (__any_sync(FULL, nV || nH)) {
             const Tap tV = tap_at<P>(vtx, vty, L, U, V), tH = tap_at<P>(htx, hty, L, U, V);
-            const Taps2 xV = load_taps(f2L, tV, g), xH = load_taps(f2L, tH, g);
-            const int4 na0 = neg64(q.x), na1 = neg64(q.y);
-            ev = sad2(xV, tV.w, na0, na1);
-            eh = sad2(xH, tH.w, na0, na1);
+            const Taps<WPL> xV = load_taps<WPL>(f2L, tV, g), xH = load_taps<WPL>(f2L, tH, g);
+            const NegQ<WPL> nq = neg_query<WPL>(q);
+            ev = sad_words<WPL>(xV, tV.w, nq);
+            eh = sad_words<WPL>(xH, tH.w, nq);
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) {
                 ev += __shfl_xor_sync(FULL, ev, o);

@@ -18,7 +18,7 @@ from . import _build
 FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_ETIMEOUT, FF_ESTATE = range(6)
 FF_FWD, FF_BWD, FF_BWD2 = 0, 1, 2
 FF_SCHED_BASIC, FF_SCHED_PLUS, FF_SCHED_PLUS_FAST, FF_SCHED_PLUS_FAST_X2 = 0, 1, 2, 3
-FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS = 1, 2, 3
+FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS, FF_DEBUG_SWEEP_WPL = 1, 2, 3, 4
 INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
@@ -27,6 +27,7 @@ EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "f
             "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
             "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy",
             "ff_batch_create", "ff_batch_run", "ff_batch_set_stream", "ff_batch_sync",
+            "ff_batch_debug_set",
             "ff_batch_launch_count", "ff_batch_last_error", "ff_batch_destroy",
             "ff_slot_bytes", "ff_server_create", "ff_server_slots", "ff_server_submit",
             "ff_server_poll", "ff_server_pending", "ff_server_launch_count",
@@ -104,6 +105,7 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_batch_run.argtypes = [P, i, ct.POINTER(ff_pair_desc), i]
         L.ff_batch_set_stream.argtypes = [P, P]
         L.ff_batch_sync.argtypes = [P]
+        L.ff_batch_debug_set.argtypes = [P, i, ct.c_longlong]
         L.ff_batch_launch_count.argtypes = [P]
         L.ff_batch_launch_count.restype = ct.c_longlong
         L.ff_batch_last_error.argtypes = [P]
@@ -478,6 +480,10 @@ def ff_batch_set_stream(b: int, stream) -> None:
 
 def ff_batch_sync(b: int) -> None:
     _bcheck(b, lib().ff_batch_sync(b))
+
+
+def ff_batch_debug_set(b: int, key: int, value: int) -> None:
+    _bcheck(b, lib().ff_batch_debug_set(b, key, value))
 
 
 def ff_batch_launch_count(b: int) -> int:

@@ -124,9 +124,9 @@ def test_every_stage_bit_exact_lab_multistrip():
     ctx.close()
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4])
+@pytest.mark.parametrize("warps,wpl", [(1, 2), (2, 2), (4, 2), (1, 1), (1, 4)])
 @pytest.mark.parametrize("C", [1, 3])
-def test_sweep_warp_variants_bit_exact(C, warps):
+def test_sweep_warp_variants_bit_exact(C, warps, wpl):
     # every CTA shape of the sweep kernel gives the oracle's result
     if C == 1:
         pair = workloads.translation_pair(seed=31, width=150, height=77)
@@ -135,6 +135,7 @@ def test_sweep_warp_variants_bit_exact(C, warps):
     S, I = 3, 5
     ctx = _ctx(C, S, I, pair.width, pair.height)
     ff.ff_debug_set(ctx.ctx, ff.FF_DEBUG_SWEEP_WARPS, warps)
+    ff.ff_debug_set(ctx.ctx, ff.FF_DEBUG_SWEEP_WPL, wpl)
     _load(ctx, pair)
     P = _params(C, S, I)
     for d, (a, b) in enumerate(((pair.img1, pair.img2), (pair.img2, pair.img1))):
