@@ -226,13 +226,21 @@ __global__ void __launch_bounds__(128)
         }
         // acc[nt] = keys of rows (lane>>2), (lane>>2)+8 and columns
         // nt*8 + 2*(lane&3) + {0, 1}: position p = 4 nt + j, row j>>1
-        float tq[2], mn[2];
+        // A key equal to the bound can only enter this lane's list while the
+        // list's own 8th key is larger: once the lane holds 8 keys at the
+        // bound, a later candidate of this lane (a larger index) at the same
+        // key loses the (key, index) order.  So equality counts only while
+        // lk[h][7] > tq[h]; in flat image regions, where thousands of
+        // candidates share one key, this keeps them off the slow path.  Keys
+        // are exact integers, so "key <= tq" is "key < tq + 1".
+        float tq[2], thr[2], mn[2];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             float v = lk[h][7];
             v = fminf(v, __shfl_xor_sync(0xffffffffu, v, 1));
             v = fminf(v, __shfl_xor_sync(0xffffffffu, v, 2));
             tq[h] = fminf(v, tinit[h]);
+            thr[h] = lk[h][7] > tq[h] ? tq[h] + 1.0f : tq[h];
             float m[NT];
 #pragma unroll
             for (int nt = 0; nt < NT; nt++) m[nt] = fminf(acc[nt][2 * h], acc[nt][2 * h + 1]);
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(128)
                 for (int nt = 0; nt < w2; nt++) m[nt] = fminf(m[nt], m[nt + w2]);
             mn[h] = m[0];
         }
-        if (__any_sync(0xffffffffu, mn[0] <= tq[0] || mn[1] <= tq[1])) {
+        if (__any_sync(0xffffffffu, mn[0] < thr[0] || mn[1] < thr[1])) {
             // slow path: the lane's candidate keys in positions, then only its hits
             float *my = &scr[warp][0][lane];
             uint32_t mask = 0;
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     my[(4 * nt + j) * 32] = acc[nt][j];
-                    mask |= (acc[nt][j] <= tq[j >> 1] ? 1u : 0u) << (4 * nt + j);
+                    mask |= (acc[nt][j] < thr[j >> 1] ? 1u : 0u) << (4 * nt + j);
                 }
             const int base = c0 + t * BN + (lane & 3) * 2;
             while (mask) {
