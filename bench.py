@@ -343,7 +343,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     ff.ff_destroy(ctx)
     return {"total_ms": total_ms, "step_ms": step_ms, "kstats": kstats, "launches": launches,
             "clocks": clocks, "e2e_s": e2e_s, "e2e_bytes": e2e_bytes, "W": W, "H": H, "C": C,
-            "S": S, "I": I, "cfg": cfg, "prm": prm, "pair": pair}
+            "S": S, "I": I, "cfg": cfg, "prm": prm, "pair": pair, "workload": args.workload}
 
 
 ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock (Tops/s)
@@ -406,15 +406,15 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
             "sizes": sorted({f"{p.width}x{p.height}" for p in pairs})}
 
 
-def recorded_traffic(kernel: str) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    sources are unchanged since it was taken."""
+def recorded_traffic(kernel: str, workload: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on this workload and the kernel's sources are unchanged since."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")) as f:
             rec = json.load(f)
         src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["sources"])
-        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"] or rec["workload"] != workload:
             return None
         return float(rec["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -447,7 +447,8 @@ def roofline(res: dict, steps: int, n_dirs: int) -> dict:
         achieved = ops_per_launch / (avg_ms / 1e3) / 1e12
         return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
                 "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
-                "traffic": recorded_traffic(dom), "launches": n_launch, "avg_launch_ms": avg_ms,
+                "traffic": recorded_traffic(dom, res["workload"]), "launches": n_launch,
+                "avg_launch_ms": avg_ms,
                 "share": share, "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2.07 GHz"}
     if dom == "k_seed_scan":
         N = 1 << (S - 1)
