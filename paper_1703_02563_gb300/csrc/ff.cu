@@ -886,7 +886,28 @@ ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L,
     k_sweep<CC, NPW, WPL><<<nstrips, SweepGeo<CC, NPW, WPL>::THREADS, 0, c->stream>>>(a)
     if (c->sweep_wpl != 2) {   // one propagation warp per strip
         if (c->C == 1) {
-            if (c->sweep_wpl == 1) FF_LAUNCH_SWEEP(1, 1, 1);
+            // gray, one word per lane: the direction compiled in (measured 5%
+            // faster per pair; for Lab the same specialisation was 2% slower)
+            if (c->sweep_wpl == 1) {
+                switch (a.d) {
+                    case 0:
+                        k_sweep<1, 1, 1, 0>
+                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
+                        break;
+                    case 1:
+                        k_sweep<1, 1, 1, 1>
+                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
+                        break;
+                    case 2:
+                        k_sweep<1, 1, 1, 2>
+                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
+                        break;
+                    default:
+                        k_sweep<1, 1, 1, 3>
+                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
+                        break;
+                }
+            }
             else FF_LAUNCH_SWEEP(1, 1, 4);
         } else {
             if (c->sweep_wpl == 1) FF_LAUNCH_SWEEP(3, 1, 1);

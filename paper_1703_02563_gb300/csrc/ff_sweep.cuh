@@ -251,7 +251,9 @@ __device__ __forceinline__ bool wait_expired(unsigned long long &t0, unsigned lo
 // Every wait is bounded and warp-uniform: a warp that sees no progress for
 // wait_ns sets the error word to FF_ETIMEOUT, raises the CTA's abort flag and
 // returns; every other wait in the CTA checks that flag on its slow path.
-template <int C, int NP, int WPL>
+// DIR >= 0 fixes the direction at compile time (it must equal a.d); -1
+// reads it from a.d.
+template <int C, int NP, int WPL, int DIR = -1>
 __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const SweepArgs a) {
     using SG = SweepGeo<C, NP, WPL>;
     constexpr int P = SG::P, G = SG::G, RW = SG::RW, R = SG::R;
@@ -336,7 +338,8 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
     const int r = w * RW + k, v = v0 + r;
     const bool row_ok = v < V;
     const int L = a.L, n = 1 << L, W = a.W, H = a.H;
-    const bool flipx = (a.d == 1 || a.d == 2), flipy = (a.d == 1 || a.d == 3);
+    const int sd = DIR >= 0 ? DIR : a.d;
+    const bool flipx = (sd == 1 || sd == 2), flipy = (sd == 1 || sd == 3);
     const int gy = row_ok ? (flipy ? V - 1 - v : v) : 0;
     const int py = gy * n;
     const int NS = U + RW - 1;                            // local steps of this warp
