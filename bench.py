@@ -273,7 +273,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
             ff.ff_region_filter(ctx, flow_f, mask, args.region, mask)
 
     for i in range(args.warmup):
-        step(i)
+        step(replica_pair_id(rank, i))
     torch.cuda.synchronize()
     ff.ff_sync(ctx)
 
@@ -292,7 +292,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
         with torch.cuda.stream(main):
             flush.fill_(i & 0xff)
         starts[i].record(main)
-        step(args.warmup + i)
+        step(replica_pair_id(rank, args.warmup + i))
         ends[i].record(main)
     torch.cuda.synchronize()
     if world > 1:
@@ -331,12 +331,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
 
     ff.ff_set_stream(ctx, main)
     for i in range(2):
-        host_step(i)
+        host_step(replica_pair_id(rank, i))
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        host_step(i)
+        host_step(replica_pair_id(rank, i))
     e2e_s = time.perf_counter() - t0
     n_out = 3 if args.two_way else 2
     e2e_bytes = (2 * C * W * H, n_out * 4 * WL * HL + WL * HL)
@@ -347,6 +347,30 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
 
 
 ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock (Tops/s)
+
+
+# ----------------------------------------------------------------------------
+# replicas (--gpus N): every rank matches its own pairs; no data-path exchange
+# ----------------------------------------------------------------------------
+def replica_pair_id(rank: int, k: int) -> int:
+    """Random-search key word of the k-th pair of a rank: ranks never share one."""
+    return rank * 1_000_000 + k
+
+
+def replica_times(times: list[float], world: int, device: str) -> list[float]:
+    """Each timing's maximum over the ranks: the job is as slow as its slowest
+    replica.  Needs an initialised process group when world > 1."""
+    if world == 1:
+        return list(times)
+    import torch
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int,
@@ -610,13 +634,7 @@ def main():
     batched = {name: run_batched(pairs, prm, args.batch_slots, args.batch_steps, 3, local_rank,
                                  args.sweep_wpl)
                for name, (pairs, prm) in batches.items()}
-    total_s = res["total_ms"] / 1e3
-    e2e_s = res["e2e_s"]
-    if world > 1:
-        import torch
-        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s, e2e_s = float(t[0]), float(t[1])
+    total_s, e2e_s = replica_times([res["total_ms"] / 1e3, res["e2e_s"]], world, "cuda")
     if rank != 0:
         if world > 1:
             import torch
@@ -624,7 +642,7 @@ def main():
         return
     K = args.steps
     pairs = K * world
-    value = pairs / total_s
+    value = replica_throughput(K, world, total_s)
     W, H, C, S, I = res["W"], res["H"], res["C"], res["S"], res["I"]
     n_dirs = 3 if args.two_way else 2
     evals_pair = n_dirs * eval_count(W, H, res["cfg"])
@@ -642,7 +660,7 @@ def main():
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
-        "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
+        "e2e": {"value": replica_throughput(K, world, e2e_s), "unit": "pairs/s",
                 "h2d_bytes_per_step": res["e2e_bytes"][0],
                 "d2h_bytes_per_step": res["e2e_bytes"][1]},
         "roofline": roofline(res, K, n_dirs),
