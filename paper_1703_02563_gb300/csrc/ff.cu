@@ -1751,7 +1751,13 @@ ff_status ff_batch_create(const ff_config *cfg, int device, int slots, void *cud
         if (e != cudaSuccess) break;
         ff_ctx *c = nullptr;
         s = ff_create(cfg, device, st, &c);
-        if (s == FF_OK) b->slot.push_back(c);
+        if (s == FF_OK) {
+            // many pairs in flight: Lab sweeps with 2 lanes of 4 words per point
+            // (fewer warp instructions per point; measured 5% more pairs/s in a
+            // 32-pair batch, 14% fewer for one pair alone)
+            if (cfg->channels == 3) c->sweep_wpl = 4;
+            b->slot.push_back(c);
+        }
     }
     if (e != cudaSuccess || s != FF_OK) {
         batch_free(b);
@@ -2040,6 +2046,7 @@ ff_status ff_server_create(const ff_config *cfg, int device, size_t mem_budget, 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.err_host, kNumDirs * sizeof(int));
         if (e == cudaSuccess) s = ff_create(cfg, device, sl.stream, &sl.ctx);
+        if (s == FF_OK && sl.ctx && cfg->channels == 3) sl.ctx->sweep_wpl = 4;   // as in ff_batch
         if (e != cudaSuccess || s != FF_OK) break;
     }
     if (e != cudaSuccess || s != FF_OK) {
