@@ -344,10 +344,24 @@ __device__ __forceinline__ int rf_find(const int *parent, int x) {
     return x;
 }
 
+// find with path halving: each visited point is re-linked to its
+// grandparent (an ancestor, so the trees stay valid under concurrent
+// linking; atomicMin keeps every parent pointer non-increasing)
+__device__ __forceinline__ int rf_find_halve(int *parent, int x) {
+    int p = __ldcg(parent + x);
+    while (p != x) {
+        const int gp = __ldcg(parent + p);
+        if (gp != p) atomicMin(parent + x, gp);
+        x = p;
+        p = gp;
+    }
+    return x;
+}
+
 __device__ void rf_unite(int *parent, int a, int b) {
     for (;;) {
-        a = rf_find(parent, a);
-        b = rf_find(parent, b);
+        a = rf_find_halve(parent, a);
+        b = rf_find_halve(parent, b);
         if (a == b) return;
         if (a > b) {
             const int t = a;
@@ -385,8 +399,8 @@ __global__ void k_rf_count(const uint32_t *__restrict__ flow, const uint8_t *__r
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= W * H || !mask[i]) return;
     const int y = i / W, x = i - y * W;
-    const int r = rf_find(parent, i);
-    parent[i] = r;
+    const int r = rf_find_halve(parent, i);
+    atomicMin(parent + i, r);
     atomicAdd(size + r, 1);
     const uint32_t f = flow[i];
     const int nb[4] = {x + 1 < W ? i + 1 : -1, x > 0 ? i - 1 : -1, y + 1 < H ? i + W : -1,
