@@ -248,12 +248,15 @@ ff_status ff_sync(ff_ctx *ctx);
  * FF_DEBUG_SWEEP_WARPS: propagation warps per sweep CTA (1, 2 or 4; default
  * 1).  FF_DEBUG_SWEEP_WPL: feature words (4 dimensions each) per lane in the
  * sweep, 1, 2 or 4 (default 1 for gray, 2 for Lab); other than 2, one
- * propagation warp per CTA.  Every value gives the same results. */
+ * propagation warp per CTA.  FF_DEBUG_SEED_TC: 1 (default) runs the seeding
+ * search's full pass on the tcgen05 tensor cores, 0 on mma.sync.  Every value
+ * gives the same results. */
 typedef enum {
     FF_DEBUG_WAIT_LIMIT_NS = 1,
     FF_DEBUG_FORCE_TIMEOUT = 2,
     FF_DEBUG_SWEEP_WARPS = 3,
-    FF_DEBUG_SWEEP_WPL = 4
+    FF_DEBUG_SWEEP_WPL = 4,
+    FF_DEBUG_SEED_TC = 5
 } ff_debug_key;
 ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
 

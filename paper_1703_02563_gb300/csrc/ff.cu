@@ -328,6 +328,7 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
 #include "ff_sweep.cuh"
 #include "ff_seed.cuh"
 #include "ff_wht_tc.cuh"
+#include "ff_seed_tc.cuh"
 
 // ---- region filter (Sec. 3.7) ------------------------------------------
 // Kept points are joined into regions by a lock-free union-find: a root only
@@ -539,6 +540,7 @@ struct DirState {
     int *qnorm = nullptr;                     //   their squared norms
     float *t0 = nullptr;                      //   upper bounds of their 8th key
     __nv_bfloat16 *cbf = nullptr;             // seeding candidates, bf16 rows of K
+    uint8_t *qtile = nullptr, *ctile = nullptr;   // the same in 128-row tensor-core tiles
     int *err = nullptr;
 };
 
@@ -569,6 +571,7 @@ struct ff_ctx {
     unsigned long long wait_ns = 2000000000ull;
     int sweep_warps = 1;   // propagation warps per sweep CTA: 1, 2 or 4
     int sweep_wpl = 2;     // feature words per lane in the sweep: 1, 2 or 4 (set by ff_create)
+    int seed_tc = 1;       // seeding full pass on tcgen05 (0: mma.sync)
     int force_timeout = 0;
     long long launches = 0;
     std::string last_error;
@@ -705,6 +708,8 @@ void free_all(ff_ctx *c) {
         cudaFree(d.qnorm);
         cudaFree(d.t0);
         cudaFree(d.cbf);
+        cudaFree(d.qtile);
+        cudaFree(d.ctile);
         cudaFree(d.err);
     }
     cudaFree(c->pair_mask);
@@ -818,19 +823,60 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
         if (s) return s;
     }
     int nchunks, chunk;
-    seed_geometry_mma(nq, ncand, &nchunks, &chunk);
-    dim3 grid((nq + 63) / 64, nchunks);
-    prof_begin(c, "k_seed_scan");
-    if (c->C == 1)
-        k_seed_mma<1><<<grid, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ncand, chunk, 1,
-                                                   W, stride, Wc, st.t0, nchunks1, nullptr,
-                                                   st.part);
-    else
-        k_seed_mma<2><<<grid, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ncand, chunk, 1,
-                                                   W, stride, Wc, st.t0, nchunks1, nullptr,
-                                                   st.part);
-    s = check_launch(c, "k_seed_scan");
-    if (s) return s;
+    if (c->seed_tc) {
+        // full pass on tcgen05: 128-row tiles of queries and candidates
+        const int K = c->C == 1 ? 16 : 32, DH2 = 9 * c->C;
+        const int nq_t = (nq + kTcRows - 1) / kTcRows;
+        const int nc_pad = (ncand + kTcRows - 1) / kTcRows * kTcRows;
+        prof_begin(c, "k_seed_prep");
+        if (K == 16) {
+            k_seed_tile<16><<<(nq_t * kTcRows * 2 + 255) / 256, 256, 0, c->stream>>>(st.qbf, nq, -1,
+                                                                                 st.qtile);
+        } else {
+            k_seed_tile<32><<<(nq_t * kTcRows * 4 + 255) / 256, 256, 0, c->stream>>>(st.qbf, nq, -1,
+                                                                                 st.qtile);
+        }
+        if ((s = check_launch(c, "k_seed_prep"))) return s;
+        prof_begin(c, "k_seed_prep");
+        if (K == 16)
+            k_seed_tile<16><<<(nc_pad * 2 + 255) / 256, 256, 0, c->stream>>>(st.cbf, ncand, DH2,
+                                                                          st.ctile);
+        else
+            k_seed_tile<32><<<(nc_pad * 4 + 255) / 256, 256, 0, c->stream>>>(st.cbf, ncand, DH2,
+                                                                          st.ctile);
+        if ((s = check_launch(c, "k_seed_prep"))) return s;
+        // one wave of two CTAs per SM (tensor memory holds two): split the
+        // candidates into 128-aligned chunks
+        int nc = (2 * 152) / nq_t;
+        nc = nc < 1 ? 1 : (nc > kMaxChunks / 2 ? kMaxChunks / 2 : nc);
+        chunk = (ncand + nc - 1) / nc;
+        chunk = (chunk + kTcRows - 1) / kTcRows * kTcRows;
+        nchunks = (ncand + chunk - 1) / chunk;
+        prof_begin(c, "k_seed_scan");
+        if (c->C == 1)
+            k_seed_tc<1><<<dim3(nq_t, nchunks), 320, tc_seed_smem_bytes<1>(), c->stream>>>(
+                st.qtile, st.qnorm, st.ctile, nq, ncand, chunk, W, stride, Wc, st.t0, nchunks1,
+                st.part, st.err, c->wait_ns);
+        else
+            k_seed_tc<2><<<dim3(nq_t, nchunks), 320, tc_seed_smem_bytes<2>(), c->stream>>>(
+                st.qtile, st.qnorm, st.ctile, nq, ncand, chunk, W, stride, Wc, st.t0, nchunks1,
+                st.part, st.err, c->wait_ns);
+        if ((s = check_launch(c, "k_seed_scan"))) return s;
+        nchunks *= 2;   // two lists per chunk
+    } else {
+        seed_geometry_mma(nq, ncand, &nchunks, &chunk);
+        dim3 grid((nq + 63) / 64, nchunks);
+        prof_begin(c, "k_seed_scan");
+        if (c->C == 1)
+            k_seed_mma<1><<<grid, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ncand, chunk,
+                                                       1, W, stride, Wc, st.t0, nchunks1, nullptr,
+                                                       st.part);
+        else
+            k_seed_mma<2><<<grid, 128, 0, c->stream>>>(st.qbf, st.qnorm, st.cbf, nq, ncand, chunk,
+                                                       1, W, stride, Wc, st.t0, nchunks1, nullptr,
+                                                       st.part);
+        if ((s = check_launch(c, "k_seed_scan"))) return s;
+    }
     prof_begin(c, "k_seed_merge");
     k_seed_merge<<<(nq + 127) / 128, 128, 0, c->stream>>>(st.part, nchunks, nq, c->cfg.seed_leaf,
                                                          st.knn_idx, st.knn_dist);
@@ -1221,6 +1267,14 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FF_ECUDA;
     DeviceGuard guard(device);
+    // the tensor-core seeding kernel takes more than 48 KB of shared memory
+    if (cudaFuncSetAttribute(k_seed_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_seed_smem_bytes<1>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_seed_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_seed_smem_bytes<2>()) != cudaSuccess) {
+        cudaGetLastError();
+        return FF_ECUDA;
+    }
     ff_ctx *c = new ff_ctx();
     c->cfg = *cfg;
     c->device = device;
@@ -1265,6 +1319,9 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
         if (e == cudaSuccess) e = alloc(&d.qnorm, c->nq_cap);
         if (e == cudaSuccess) e = alloc(&d.t0, c->nq_cap * kMaxChunks);
         if (e == cudaSuccess) e = alloc(&d.cbf, npix * K);
+        const size_t pad = kTcRows;
+        if (e == cudaSuccess) e = alloc(&d.qtile, (c->nq_cap + pad - 1) / pad * pad * K * 2);
+        if (e == cudaSuccess) e = alloc(&d.ctile, (npix + pad - 1) / pad * pad * K * 2);
         if (e == cudaSuccess) e = alloc(&d.err, 1);
         if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int));
     }
@@ -1585,6 +1642,9 @@ ff_status ff_debug_set(ff_ctx *c, ff_debug_key key, long long value) {
             if (value != 1 && value != 2 && value != 4)
                 return fail(c, FF_EINVAL, "sweep warps must be 1, 2 or 4");
             c->sweep_warps = (int)value;
+            return FF_OK;
+        case FF_DEBUG_SEED_TC:
+            c->seed_tc = value != 0;
             return FF_OK;
         case FF_DEBUG_SWEEP_WPL:
             if (value != 1 && value != 2 && value != 4)

@@ -70,16 +70,19 @@ def test_features_bit_exact(C, W, H, S):
     ctx.close()
 
 
+@pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("C,W,H,S,stride", [(1, 128, 96, 3, 1), (3, 97, 71, 3, 2),
                                             (1, 45, 33, 2, 1), (3, 20, 12, 1, 3),
-                                            (3, 200, 120, 3, 1), (1, 301, 77, 2, 1)])
-def test_seed_knn_bit_exact(C, W, H, S, stride):
+                                            (3, 200, 120, 3, 1), (1, 301, 77, 2, 1),
+                                            (3, 320, 240, 4, 1)])
+def test_seed_knn_bit_exact(C, W, H, S, stride, tc):
     if C == 1:
         pair = workloads.translation_pair(seed=W, width=W, height=H) if W >= 64 else \
             workloads.random_pair(seed=W, width=W, height=H, channels=1)
     else:
         pair = workloads.layered_pair(seed=W, width=W, height=H, channels=3, max_disp=12)
     ctx = _ctx(C, S, 1, W, H, stride=stride)
+    ff.ff_debug_set(ctx.ctx, ff.FF_DEBUG_SEED_TC, tc)
     _load(ctx, pair)
     f1 = O.features_all(pair.img1, S)
     f2 = O.features_all(pair.img2, S)
