@@ -234,6 +234,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
         ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WARPS, args.sweep_warps)
     if args.sweep_wpl:
         ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WPL, args.sweep_wpl)
+    if args.seed_path == "mma":
+        ff.ff_debug_set(ctx, ff.FF_DEBUG_SEED_TC, 0)
     img1 = torch.from_numpy(pair.img1).to(dev)
     img2 = torch.from_numpy(pair.img2).to(dev)
     flow_f = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
@@ -552,6 +554,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--sweep-warps", type=int, default=0,
                     help="propagation warps per sweep CTA (1, 2, 4; 0 = library default)")
+    ap.add_argument("--seed-path", choices=["tc", "mma"], default="tc",
+                    help="seeding full pass on tcgen05 (default) or mma.sync")
     ap.add_argument("--sweep-wpl", type=int, default=0,
                     help="feature words per lane in the sweep (1, 2, 4; 0 = library default)")
     args = ap.parse_args()
