@@ -2010,9 +2010,11 @@ size_t context_bytes(const ff_config &cfg) {
     size_t b = 2 * level_offset(cfg.max_width, cfg.max_height, P, cfg.scales);   // features
     b += 2 * npix * C + 3 * npix * 4 + npix;                                    // staging
     b += npix * (4 + 4 + 1);                                                    // region scratch
+    const size_t pad = kTcRows;
     const size_t dir = npix * 4 * 4 + edge * 8 + FF_MAX_SCALES * kMaxIters * 4 +
                        nq * FF_MAX_LEAF * 8 + nq * kMaxChunks * 8 * 8 + nq * K * 2 + nq * 4 +
-                       nq * kMaxChunks * 4 + npix * K * 2 + 4;
+                       nq * kMaxChunks * 4 + npix * K * 2 + 4 +
+                       ((nq + pad - 1) / pad + (npix + pad - 1) / pad) * pad * K * 2;   // tiles
     return b + kNumDirs * dir;
 }
 

@@ -83,3 +83,18 @@ def test_open_loop_run_retires_every_request():
     assert res["p99_ms"] >= res["p50_ms"] > 0
     assert len(pool.free) == 6
     ff.ff_server_destroy(srv)
+
+
+def test_slot_bytes_match_what_a_context_allocates():
+    # admission by device memory is only as good as this estimate
+    import torch
+    cfg = ff.Config(channels=3, scales=4, iters=6, max_width=1024, max_height=436)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ctx = ff.ff_create(cfg, 0)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    used = free0 - free1
+    est = ff.ff_slot_bytes(cfg)
+    ff.ff_destroy(ctx)
+    assert abs(used - est) <= 0.05 * est + (8 << 20), (used, est)
