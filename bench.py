@@ -376,7 +376,7 @@ def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float
 
 
 def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int,
-                sweep_wpl: int = 0) -> dict:
+                sweep_wpl: int = 0, autotune: bool = False) -> dict:
     """Throughput of the batched form on `pairs` (inputs resident, L2
     flushed between steps, one graph launch per step timed with CUDA events
     on the batch's stream)."""
@@ -390,9 +390,6 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
     cfg = ff.Config(channels=prm["channels"], scales=prm["scales"], iters=prm["iters"],
                     radius_q3=prm["radius_q3"], max_width=W, max_height=H)
     stream = torch.cuda.Stream(dev)
-    b = ff.ff_batch_create(cfg, local_rank, slots=slots, stream=stream)
-    if sweep_wpl:
-        ff.ff_batch_debug_set(b, ff.FF_DEBUG_SWEEP_WPL, sweep_wpl)
     imgs = [(torch.from_numpy(p.img1).to(dev), torch.from_numpy(p.img2).to(dev)) for p in pairs]
     outs = [tuple(torch.empty(s, dtype=t, device=dev)
                   for s, t in (((p.height, p.width, 2), torch.int16),
@@ -401,6 +398,14 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
     descs = ff.pair_descs([dict(img1=i1, img2=i2, w=p.width, h=p.height, pair_id=k,
                                 flow_fwd=o[0], flow_bwd=o[1], mask=o[2])
                            for k, (p, (i1, i2), o) in enumerate(zip(pairs, imgs, outs))])
+    tuned = None
+    if autotune:
+        from paper_1703_02563_gb300 import autotune as at
+        tuned = at.tune(cfg, descs, len(pairs), local_rank)
+        slots, sweep_wpl = tuned["slots"], tuned["wpl"]
+    b = ff.ff_batch_create(cfg, local_rank, slots=slots, stream=stream)
+    if sweep_wpl:
+        ff.ff_batch_debug_set(b, ff.FF_DEBUG_SWEEP_WPL, sweep_wpl)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(warmup):
         ff.ff_batch_run(b, descs, use_graph=True)
@@ -429,7 +434,8 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
             "evals_per_s": evals / total_s, "gpu_launches": launches,
             # a lower bound on k_sweep's ALU fraction: all of the step's time charged to it
             "sweep_alu_frac_of_step": sweep_ops / total_s / 1e12 / ALU_PEAK_TOPS,
-            "sizes": sorted({f"{p.width}x{p.height}" for p in pairs})}
+            "sizes": sorted({f"{p.width}x{p.height}" for p in pairs}),
+            **({"autotune": tuned} if tuned else {})}
 
 
 def recorded_traffic(kernel: str, workload: str) -> float | None:
@@ -552,6 +558,9 @@ def main():
     ap.add_argument("--batch-slots", type=int, default=32,
                     help="matching slots of the batched legs (0 = skip them)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose each batched leg's slots and sweep lane layout by timing "
+                         "(autotune.py; the choice is cached)")
     ap.add_argument("--sweep-warps", type=int, default=0,
                     help="propagation warps per sweep CTA (1, 2, 4; 0 = library default)")
     ap.add_argument("--seed-path", choices=["tc", "mma"], default="tc",
@@ -636,7 +645,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world, local_rank)
     batched = {name: run_batched(pairs, prm, args.batch_slots, args.batch_steps, 3, local_rank,
-                                 args.sweep_wpl)
+                                 args.sweep_wpl, args.autotune)
                for name, (pairs, prm) in batches.items()}
     total_s, e2e_s = replica_times([res["total_ms"] / 1e3, res["e2e_s"]], world, "cuda")
     if rank != 0:

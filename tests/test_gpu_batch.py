@@ -149,3 +149,19 @@ def test_batch_rejects_bad_descriptors_before_launching():
     ff.ff_batch_run(b, [])
     ff.ff_batch_sync(b)
     ff.ff_batch_destroy(b)
+
+
+def test_autotune_times_every_candidate_and_keeps_the_fastest(tmp_path):
+    from paper_1703_02563_gb300 import autotune
+    pairs = [workloads.batch_pair(13, k, SMALL_SIZES) for k in range(4)]
+    cfg = ff.Config(channels=3, scales=3, iters=4, radius_q3=8, max_width=128, max_height=96)
+    imgs = _upload(pairs)
+    outs = _outputs(pairs, cfg, [False] * 4)
+    descs = ff.pair_descs(_descs(pairs, imgs, outs))
+    cache = str(tmp_path / "tune.json")
+    res = autotune.tune(cfg, descs, 4, max_slots=16, steps=1, path=cache)
+    cands = autotune.candidates(cfg, 16)
+    assert [(t["slots"], t["wpl"]) for t in res["trials"]] == cands
+    assert all(t["ms"] > 0 for t in res["trials"])
+    assert res["ms"] == min(t["ms"] for t in res["trials"])
+    assert autotune.lookup(cfg, 0, cache)["slots"] == res["slots"]
