@@ -342,8 +342,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     e2e_s = time.perf_counter() - t0
     n_out = 3 if args.two_way else 2
     e2e_bytes = (2 * C * W * H, n_out * 4 * WL * HL + WL * HL)
+    accuracy = flow_accuracy(flow_f.cpu().numpy(), mask.cpu().numpy(), pair, cfg.final_level())
     ff.ff_destroy(ctx)
     return {"total_ms": total_ms, "step_ms": step_ms, "kstats": kstats, "launches": launches,
+            "accuracy": accuracy,
             "clocks": clocks, "e2e_s": e2e_s, "e2e_bytes": e2e_bytes, "W": W, "H": H, "C": C,
             "S": S, "I": I, "cfg": cfg, "prm": prm, "pair": pair, "workload": args.workload}
 
@@ -354,6 +356,25 @@ ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock
 # ----------------------------------------------------------------------------
 # replicas (--gpus N): every rank matches its own pairs; no data-path exchange
 # ----------------------------------------------------------------------------
+def flow_accuracy(flow_q3: np.ndarray, mask: np.ndarray, pair, level: int = 0) -> dict:
+    """End-point error of a forward flow (1/8 px, on the level-`level` grid)
+    against the generator's ground truth, over all points, the visible ones
+    (not occluded) and the ones the filter kept; and the kept fraction."""
+    n = 1 << level
+    gt = pair.flow[::n, ::n][:flow_q3.shape[0], :flow_q3.shape[1]]
+    occ = pair.occ[::n, ::n][:flow_q3.shape[0], :flow_q3.shape[1]]
+    valid = flow_q3[..., 0] != -32768
+    f = flow_q3.astype(np.float64) / 8.0
+    err = np.hypot(f[..., 0] - gt[..., 0], f[..., 1] - gt[..., 1])
+    kept = (mask != 0) & valid
+    vis = valid & ~occ
+    mean = lambda m: float(err[m].mean()) if m.any() else None
+    return {"epe_all": mean(valid), "epe_visible": mean(vis), "epe_kept": mean(kept),
+            "kept_fraction": float(kept.mean()),
+            "outliers_3px_visible": float((err[vis] > 3.0).mean()) if vis.any() else None,
+            "outliers_3px_kept": float((err[kept] > 3.0).mean()) if kept.any() else None}
+
+
 def replica_pair_id(rank: int, k: int) -> int:
     """Random-search key word of the k-th pair of a rank: ranks never share one."""
     return rank * 1_000_000 + k
@@ -678,6 +699,7 @@ def main():
                 "d2h_bytes_per_step": res["e2e_bytes"][1]},
         "roofline": roofline(res, K, n_dirs),
         "kernels_ms": {k: round(v[1], 4) for k, v in res["kstats"].items() if v[0]},
+        "accuracy": res["accuracy"],
     }
     if batched:
         line["batched"] = batched
