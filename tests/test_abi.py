@@ -75,3 +75,12 @@ def test_server_admission_by_memory_needs_no_gpu():
     c = cfg.c()
     assert ff.lib().ff_server_create(ct.byref(c), 0, per - 1, 8, ct.byref(out)) == ff.FF_ENOMEM
     assert out.value is None
+
+
+def test_config_limits_are_checked_before_any_device_call():
+    out = ct.c_void_p()
+    for field, value in (("max_width", 4097), ("max_height", 0), ("scales", 9), ("iters", 65),
+                         ("schedule", 4), ("channels", 2)):
+        c = ff.Config(**{field: value}).c()
+        assert ff.lib().ff_create(ct.byref(c), 0, None, ct.byref(out)) == ff.FF_EINVAL, field
+        assert out.value is None

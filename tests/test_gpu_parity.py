@@ -159,6 +159,10 @@ FULL_CASES = [
     ("gray1x7", lambda: workloads.random_pair(seed=7, width=1, height=7), 1, 1, 2, 8),
     ("gray1x1", lambda: workloads.random_pair(seed=8, width=1, height=1), 1, 1, 2, 8),
     ("lab2x3", lambda: workloads.random_pair(seed=9, width=2, height=3, channels=3), 3, 2, 3, 8),
+    # the largest frame side the library takes (4096), as a thin strip
+    ("gray4096x9", lambda: workloads.random_pair(seed=10, width=4096, height=9), 1, 2, 2, 8),
+    ("lab5x4096", lambda: workloads.random_pair(seed=11, width=5, height=4096, channels=3), 3, 2,
+     2, 8),
 ]
 
 
