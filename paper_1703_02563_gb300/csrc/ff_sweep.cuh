@@ -22,7 +22,7 @@ struct SweepArgs {
 
 // Lane layout: G lanes per grid point, WPL 4-dimension feature words per
 // lane; RW = 32/G rows per warp; NP propagation warps per strip, each paired
-// with a helper warp; one loader warp.
+// with a helper warp and a warming warp; one loader warp.
 template <int C, int NP_, int WPL_ = 2> struct SweepGeo {
     static constexpr int P = Geo<C>::P;
     static constexpr int WPL = WPL_;     // feature words per lane: 1, 2 or 4
@@ -40,7 +40,7 @@ template <int C, int NP_, int WPL_ = 2> struct SweepGeo {
     static constexpr int PD = 1;         // L1 warming distance (level pixels)
     static constexpr int PF_COLS = 4;    // feature columns warmed from the target on
     static constexpr int PF_ROWS = 4;    // feature rows warmed around the target
-    static constexpr int THREADS = (2 * NP + 1) * 32;
+    static constexpr int THREADS = (3 * NP + 1) * 32;   // + loader, + NP warming warps
 };
 
 template <int WPL> struct QWords {
@@ -245,6 +245,10 @@ __device__ __forceinline__ bool wait_expired(unsigned long long &t0, unsigned lo
 //    (y*W + x, t, L, dir), key (seed, pair_id); accepted only if strictly
 //    better) and writes the final flow and cost to memory.  Neighbours in
 //    this sweep see only the sweep value, never the random-search result.
+//  * Each propagation warp has a warming warp too.  It follows the result
+//    slots and warms L1 with the feature sectors around the target of each
+//    decided flow two points further on, where the next loads of that row
+//    will most likely fall.
 //  * A candidate equal to the current flow has exactly the cached cost, and
 //    equal candidates have equal costs, so such evaluations are skipped
 //    (warp-uniformly) without changing any result.
@@ -331,8 +335,9 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
         return;
     }
 
-    const bool helper = warp >= NP;
-    const int w = helper ? warp - NP : warp;
+    const bool warmer = warp > 2 * NP;
+    const bool helper = !warmer && warp >= NP;
+    const int w = warmer ? warp - 2 * NP - 1 : (helper ? warp - NP : warp);
     if (v0 + w * RW >= V) return;                         // no valid row in this warp
     const int k = lane / G, g = lane - (lane / G) * G;
     const int r = w * RW + k, v = v0 + r;
@@ -345,6 +350,60 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
     const int NS = U + RW - 1;                            // local steps of this warp
     const uint8_t *f1L = a.f1L, *f2L = a.f2L;
     const size_t rowbase = (size_t)gy * U;
+
+    if (warmer) {
+        // ================= warming warp =================
+        // Warms L1 with the feature sectors its propagation warp will read two
+        // points after each decision: rows iy-1 .. iy+2 around the target of
+        // the decided flow at that point (one row per lane), columns ix ..
+        // ix+PF_COLS-1, one sector (one point's feature vector) each, by
+        // asynchronous 4-byte copies into a scratch word.  Features are read
+        // in 32-byte sectors, so each step needs new ones; one step of lead
+        // covers the L2 latency, and the nearer the point, the likelier the
+        // decided flow is still the latest one (measured: 1 step and 4
+        // columns beat 16 steps and 1 column by 18%).  It follows the tagged
+        // result slots the propagation warp publishes every step, so the
+        // propagation warp spends no instruction on it; a slot holding a
+        // later step than expected (this warp fell a ring behind) is taken
+        // as it is.
+        const int sxdir = flipx ? -1 : 1;
+        const int half = n >> 1;
+        int i = 0;
+        unsigned long long t0 = 0;
+        while (i < NS) {
+            const unsigned long long e = lds64(&sm.out[w][i & (DO - 1)][k]);
+            const uint32_t d = ((uint32_t)(e >> 52) - (uint32_t)i) & 0xFFFu;   // its step - i
+            if (!__all_sync(FULL, d < 0x800u)) {
+                if (wait_expired(t0, a.wait_ns, v_abort, a.err)) break;
+                continue;
+            }
+            t0 = 0;
+            const int u = i + (int)d - k;                 // the point decided in that step
+            const uint32_t f = (uint32_t)e;
+            if (row_ok && u >= 0 && u < U && f != kFlowInvalid && g < PF_ROWS) {
+                const int gx = flipx ? U - 1 - u : u;
+                int tx, ty;
+                target_of(f, (gx + sxdir * (PD + 1)) * n, py, W, H, tx, ty);
+                const int ix = min((tx + half) >> (L + 3), U - 1);
+                const int iy0 = ((ty + half) >> (L + 3)) - 1;
+#pragma unroll
+                for (int rr = 0; rr < (PF_ROWS + G - 1) / G; rr++) {
+                    const int row = g + rr * G;
+                    if (row < PF_ROWS) {
+                        const uint8_t *rowp = f2L + (size_t)clampi(iy0 + row, 0, V - 1) * U * P;
+#pragma unroll
+                        for (int cc = 0; cc < PF_COLS; cc++)
+                            cp_async4(&sm.pf_sink[w][lane],
+                                      rowp + (size_t)min(ix + cc, U - 1) * P);
+                    }
+                }
+            }
+            i += 1 + (int)__reduce_min_sync(FULL, d);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        return;
+    }
 
     if (helper) {
         // ================= helper warp =================
@@ -456,7 +515,6 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
     const bool ring_out = (w < NP - 1) && (v0 + (w + 1) * RW < V);
     const bool edge_out = (w == NP - 1) && (k == RW - 1) && (strip + 1 < nstrips);
     const bool top_src = (v0 + w * RW) > 0;     // group 0 has a row above it
-    const int sxdir = flipx ? -1 : 1;
     uint32_t last = kFlowInvalid;       // this row's sweep value at the previous step
     int ready = 0;                      // cached in_ready
     int ocons = 0;                      // cached out_cons
@@ -467,31 +525,6 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
         const int gx = flipx ? U - 1 - u : u;
         const int px = gx * n;
         const uint32_t above = __shfl_up_sync(FULL, last, G);
-        // Warm L1 with the feature sectors this row will read PD steps from now:
-        // rows iy-1 .. iy+2 around the target of its latest flow (one row per
-        // lane), columns ix .. ix+PF_COLS-1, one sector (one point's feature
-        // vector) each, by asynchronous 4-byte copies into a scratch word.
-        // Features are read in 32-byte sectors, so each step needs new ones;
-        // one step of lead covers the L2 latency, and the nearer the point,
-        // the likelier its flow is still the latest one (measured: 1 step and
-        // 4 columns beat 16 steps and 1 column by 18%).
-        if (active && last != kFlowInvalid && g < PF_ROWS) {
-            int tx, ty;
-            target_of(last, px + sxdir * PD * n, py, W, H, tx, ty);
-            const int half = n >> 1;
-            const int ix = min((tx + half) >> (L + 3), U - 1);
-            const int iy0 = ((ty + half) >> (L + 3)) - 1;
-#pragma unroll
-            for (int rr = 0; rr < (PF_ROWS + G - 1) / G; rr++) {
-                const int row = g + rr * G;
-                if (row < PF_ROWS) {
-                    const uint8_t *rowp = f2L + (size_t)clampi(iy0 + row, 0, V - 1) * U * P;
-#pragma unroll
-                    for (int cc = 0; cc < PF_COLS; cc++)
-                        cp_async4(&sm.pf_sink[w][lane], rowp + (size_t)min(ix + cc, U - 1) * P);
-                }
-            }
-        }
         // staged inputs of step i, and (group 0) the vertical source of column i
         const bool need_top = top_src && i < U && k == 0;
         const unsigned long long *tslot =
