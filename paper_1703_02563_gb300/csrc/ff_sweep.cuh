@@ -39,7 +39,7 @@ template <int C, int NP_, int WPL_ = 2> struct SweepGeo {
     static constexpr int NB = 8 / G;     // random-search offsets per lane per 8 steps
     static constexpr int PD = 1;         // L1 warming distance (level pixels)
     static constexpr int PF_COLS = 4;    // feature columns warmed from the target on
-    static constexpr int PF_ROWS = 4;    // feature rows warmed around the target
+    static constexpr int PF_ROWS = 6;    // feature rows warmed around the target
     static constexpr int THREADS = (3 * NP + 1) * 32;   // + loader, + NP warming warps
 };
 
@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
     if (warmer) {
         // ================= warming warp =================
         // Warms L1 with the feature sectors its propagation warp will read two
-        // points after each decision: rows iy-1 .. iy+2 around the target of
-        // the decided flow at that point (one row per lane), columns ix ..
+        // points after each decision: rows iy-2 .. iy+3 around the target of
+        // the decided flow at that point (a row per lane), columns ix ..
         // ix+PF_COLS-1, one sector (one point's feature vector) each, by
         // asynchronous 4-byte copies into a scratch word.  Features are read
         // in 32-byte sectors, so each step needs new ones; one step of lead
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
                 int tx, ty;
                 target_of(f, (gx + sxdir * (PD + 1)) * n, py, W, H, tx, ty);
                 const int ix = min((tx + half) >> (L + 3), U - 1);
-                const int iy0 = ((ty + half) >> (L + 3)) - 1;
+                const int iy0 = ((ty + half) >> (L + 3)) - (PF_ROWS / 2 - 1);
 #pragma unroll
                 for (int rr = 0; rr < (PF_ROWS + G - 1) / G; rr++) {
                     const int row = g + rr * G;
