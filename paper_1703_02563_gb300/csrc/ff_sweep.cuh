@@ -566,8 +566,10 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
         const uint32_t cH = pack_flow(htx - 8 * px, hty - 8 * py);
         const bool nV = active && vv && cV != cur;
         const bool nH = active && hv && cH != cur && !(vv && cH == cV);
+        // each candidate is evaluated when some row of the warp needs it
+        const bool anyV = __any_sync(FULL, nV), anyH = __any_sync(FULL, nH);
         int ev = 0, eh = 0;
-        if (__any_sync(FULL, nV || nH)) {
+        if (anyV && anyH) {
             const Tap tV = tap_at<P>(vtx, vty, L, U, V), tH = tap_at<P>(htx, hty, L, U, V);
             const Taps<WPL> xV = load_taps<WPL>(f2L, tV, g), xH = load_taps<WPL>(f2L, tH, g);
             const NegQ<WPL> nq = neg_query<WPL>(q);
@@ -578,6 +580,16 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
                 ev += __shfl_xor_sync(FULL, ev, o);
                 eh += __shfl_xor_sync(FULL, eh, o);
             }
+        } else if (anyV || anyH) {
+            const Tap t1 = anyV ? tap_at<P>(vtx, vty, L, U, V) : tap_at<P>(htx, hty, L, U, V);
+            const Taps<WPL> x1 = load_taps<WPL>(f2L, t1, g);
+            int e1 = sad_words<WPL>(x1, t1.w, neg_query<WPL>(q));
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) e1 += __shfl_xor_sync(FULL, e1, o);
+            if (anyV)
+                ev = e1;
+            else
+                eh = e1;
         }
         // [current, vertical, horizontal]: lowest cost, the later one on ties
         uint32_t best = cur;
@@ -594,17 +606,19 @@ __global__ void __launch_bounds__(SweepGeo<C, NP, WPL>::THREADS) k_sweep(const S
         }
         if (active) last = best;
         // hand the last row's value down (next warp, next strip)
-        const bool pub = ring_out && active && k == RW - 1;
-        if (__any_sync(FULL, pub && ncons <= u - RING)) {
-            unsigned long long t1 = 0;
-            while (true) {
-                if (pub && ncons <= u - RING) ncons = v_cons[w + 1];
-                if (__all_sync(FULL, !pub || ncons > u - RING)) break;
-                if (wait_expired(t1, a.wait_ns, v_abort, a.err)) return;
+        if constexpr (NP > 1) {
+            const bool pub = ring_out && active && k == RW - 1;
+            if (__any_sync(FULL, pub && ncons <= u - RING)) {
+                unsigned long long t1 = 0;
+                while (true) {
+                    if (pub && ncons <= u - RING) ncons = v_cons[w + 1];
+                    if (__all_sync(FULL, !pub || ncons > u - RING)) break;
+                    if (wait_expired(t1, a.wait_ns, v_abort, a.err)) return;
+                }
             }
+            if (pub && g == 0)
+                sts64(&sm.ring[w][u & (RING - 1)], ((unsigned long long)(u + 1) << 32) | best);
         }
-        if (pub && g == 0)
-            sts64(&sm.ring[w][u & (RING - 1)], ((unsigned long long)(u + 1) << 32) | best);
         if (edge_out && active && g == 0)
             st_relaxed_u64(a.edge + (size_t)strip * U + u,
                            ((unsigned long long)a.epoch << 32) | best);
