@@ -39,7 +39,7 @@ template <int C, int NP_, int WPL_ = 2> struct SweepGeo {
     static constexpr int NB = 8 / G;     // random-search offsets per lane per 8 steps
     static constexpr int PD = 1;         // L1 warming distance (level pixels)
     static constexpr int PF_COLS = 4;    // feature columns warmed from the target on
-    static constexpr int PF_ROWS = 6;    // feature rows warmed around the target
+    static constexpr int PF_ROWS = WPL == 4 ? 4 : 6;   // feature rows warmed around the target
     static constexpr int THREADS = (3 * NP + 1) * 32;   // + loader, + NP warming warps
 };
 
