@@ -1,0 +1,58 @@
+"""bench.py's host-side arithmetic (CPU): the evaluation count behind
+``evals_per_s`` and the sweep roofline, and the roofline record itself.
+
+The count is a restatement in the benchmark of how many matching-error
+evaluations one direction performs; here it must equal the number the oracle
+counts while it runs the method, for every schedule and for frames with
+ragged coarse levels.
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+import pytest
+
+import oracle as O
+from paper_1703_02563_gb300 import ff, workloads
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
+@pytest.mark.parametrize("W,H,S,iters,leaf,stride", [
+    (45, 31, 3, 4, 8, 1),
+    (33, 17, 4, 6, 4, 1),
+    (40, 26, 3, 5, 8, 2),
+])
+def test_eval_count_equals_the_oracles_count(schedule, W, H, S, iters, leaf, stride):
+    if schedule == 3 and S < 3:
+        pytest.skip("Fast x2 needs three scales")
+    pair = workloads.random_pair(seed=W * H + schedule, width=W, height=H)
+    P = O.Params(scales=S, iters=iters, seed_leaf=leaf, seed_stride=stride, schedule=schedule)
+    _, _, counted = O.match(P, pair.img1, pair.img2, 0, 0)
+    cfg = ff.Config(channels=1, scales=S, iters=iters, seed_leaf=leaf, seed_stride=stride,
+                    schedule=schedule)
+    assert bench.eval_count(W, H, cfg) == counted
+
+
+def test_sweep_roofline_arithmetic():
+    # one direction's sweeps on a 64x48 frame, timed as 10 launches of 2 ms
+    cfg = ff.Config(channels=3, scales=2, iters=5)
+    W, H = 64, 48
+    res = {"kstats": {"k_sweep": (10, 20.0), "k_features": (2, 0.5)},
+           "W": W, "H": H, "C": 3, "S": 2, "I": 5, "cfg": cfg, "workload": "none"}
+    r = bench.roofline(res, steps=1, n_dirs=1)
+    evals = bench.sweep_evals(W, H, cfg)
+    # by hand: level 0 64x48, level 1 32x24; 5 sweeps (2 candidates per point, one
+    # fewer per incoming border point) and 4 random searches per level
+    by_hand = sum(5 * (2 * w * h - w - h) + 4 * w * h for w, h in ((64, 48), (32, 24)))
+    assert evals == by_hand
+    ops_per_launch = evals * 27 * 10 / 10
+    assert r["kernel"] == "k_sweep" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(ops_per_launch / 2e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["share"] == pytest.approx(20.0 / 20.5)
+    assert r["traffic"] is None          # no recorded capture for this workload
+    assert r["peak"] == pytest.approx(152 * 64 * 2.07e9 / 1e12)
