@@ -454,6 +454,49 @@ def periodic_pair(seed: int = 5, width: int = 95, height: int = 95, period: int 
     return FramePair(f1[None], f2[None], flow, occ, f"periodic{width}x{height}")
 
 
+def periodic_object_pair(seed: int = 5, width: int = 95, height: int = 95, size: int = 36,
+                         period: int = 12, shift=(11, 6), bg_shift=(2, 1),
+                         sigma: float = 1.5) -> FramePair:
+    """A square object with a repetitive texture, moving on its own.
+
+    A stand-in for the paper's repetitive-pattern experiment (Sec. 4.5, 95x95
+    frames): the object's texture is a random tile repeated with ``period``,
+    so a window smaller than the object matches it at every period shift; the
+    object (``size`` x ``size``) is smaller than the coarsest influence area
+    of a 4-scale run.  The background is smoothed noise translated by
+    ``bg_shift``; the object moves by ``shift`` and covers the background in
+    both frames.
+    """
+    rng = np.random.default_rng(seed)
+    pad = 48
+    noise = ndimage.gaussian_filter(rng.standard_normal((height + 2 * pad, width + 2 * pad)),
+                                    sigma, mode="wrap")
+    bg = _to_u8((noise - noise.min()) / (noise.max() - noise.min()))
+    tile = ndimage.gaussian_filter(rng.random((period, period)), 1.0, mode="wrap")
+    tile = (tile - tile.min()) / (tile.max() - tile.min())
+    reps = size // period + 2
+    obj = _to_u8(np.tile(tile, (reps, reps))[:size, :size])
+    bx, by = bg_shift
+    ox, oy = shift
+    f1 = bg[pad:pad + height, pad:pad + width].copy()
+    f2 = bg[pad - by:pad - by + height, pad - bx:pad - bx + width].copy()
+    x0 = (width - size) // 2 - ox // 2
+    y0 = (height - size) // 2 - oy // 2
+    assert 0 <= x0 and x0 + size + max(ox, 0) <= width and x0 + min(ox, 0) >= 0
+    assert 0 <= y0 and y0 + size + max(oy, 0) <= height and y0 + min(oy, 0) >= 0
+    f1[y0:y0 + size, x0:x0 + size] = obj
+    f2[y0 + oy:y0 + oy + size, x0 + ox:x0 + ox + size] = obj
+    yy, xx = np.mgrid[0:height, 0:width]
+    inobj = (xx >= x0) & (xx < x0 + size) & (yy >= y0) & (yy < y0 + size)
+    flow = np.zeros((height, width, 2))
+    flow[..., 0], flow[..., 1] = bx, by
+    flow[inobj, 0], flow[inobj, 1] = ox, oy
+    tx, ty = xx + flow[..., 0].astype(int), yy + flow[..., 1].astype(int)
+    covered = ((tx >= x0 + ox) & (tx < x0 + ox + size) & (ty >= y0 + oy) & (ty < y0 + oy + size))
+    occ = (tx < 0) | (tx >= width) | (ty < 0) | (ty >= height) | (~inobj & covered)
+    return FramePair(f1[None], f2[None], flow, occ, f"periodic_object{width}x{height}")
+
+
 def random_pair(seed: int, width: int, height: int, channels: int = 1) -> FramePair:
     """Two independent uniform-noise frames (no meaningful flow); for parity cases."""
     rng = np.random.default_rng(seed)

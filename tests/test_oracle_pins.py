@@ -811,3 +811,184 @@ def test_sparsify_level1_reads_the_nearest_grid_point():
     m = np.ones((1, 2), np.uint8)
     np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 2, 1, level=1), [[0, 1]])
     np.testing.assert_array_equal(O.sparsify(fwd, b1, None, m, 2, 1, level=0), [[1, 0]])
+
+
+# --------------------------------------------------------------------------
+# exhaustive matching (Sec. 4: the exact nearest-neighbour field) and the
+# Eq. 1 rerank.  The exhaustive cost table is built here with scipy's bilinear
+# interpolation, independently of the oracle's cost function.
+# --------------------------------------------------------------------------
+def _exhaustive_table(f2L: np.ndarray, W: int, H: int) -> np.ndarray:
+    """64 x the bilinear interpolation of level-0 features at every Q3 target
+    inside the frame: int32 [8(H-1)+1][8(W-1)+1][D]."""
+    ty, tx = np.mgrid[0:8 * (H - 1) + 1, 0:8 * (W - 1) + 1]
+    coords = np.stack([ty.ravel() / 8.0, tx.ravel() / 8.0])
+    D = f2L.shape[-1]
+    out = np.empty(ty.shape + (D,), np.int32)
+    for d in range(D):
+        v = ndimage.map_coordinates(f2L[..., d].astype(np.float64), coords, order=1,
+                                    mode="nearest")
+        out[..., d] = np.rint(64.0 * v).reshape(ty.shape).astype(np.int32)
+    return out
+
+
+def _costs_at(table: np.ndarray, f1L: np.ndarray, px: int, py: int) -> np.ndarray:
+    """E(p, t) for every Q3 target t of the table: int64 [TY][TX]."""
+    q = 64 * f1L[py, px].astype(np.int32)
+    return np.abs(table - q).sum(axis=-1, dtype=np.int64)
+
+
+def _flow_index(px, py, fx, fy):
+    return 8 * py + int(fy), 8 * px + int(fx)
+
+
+@pytest.mark.parametrize("C,W,H,S", [(1, 32, 24, 1), (1, 31, 23, 3), (3, 24, 20, 2),
+                                     (3, 32, 24, 3)])
+def test_final_costs_against_exhaustive_search(C, W, H, S):
+    # every final flow's cached cost is the independently computed E of that
+    # flow, and no point ends below the global minimum over all Q3 targets
+    pair = workloads.layered_pair(seed=40 + C + S, width=W, height=H, channels=C, max_disp=6.0)
+    P = O.Params(channels=C, scales=S, iters=4)
+    f1 = O.features_all(pair.img1, S)
+    f2 = O.features_all(pair.img2, S)
+    flow, cost, _ = O.match_features(P, f1, f2, W, H, 0, 3)
+    table = _exhaustive_table(f2[0], W, H)
+    for py in range(H):
+        for px in range(W):
+            E = _costs_at(table, f1[0], px, py)
+            fx, fy = flow[py, px]
+            assert fx != O.INVALID
+            iy, ix = _flow_index(px, py, fx, fy)
+            assert 0 <= iy < E.shape[0] and 0 <= ix < E.shape[1]
+            assert cost[py, px] == E[iy, ix]
+            assert cost[py, px] >= E.min()
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_translation_is_the_unique_exhaustive_minimum_and_is_found(C):
+    # on smoothed noise under an integer translation the true flow costs 0 and
+    # is the only zero of E on the interior: the exact nearest-neighbour field,
+    # and the method's result, are that flow
+    W, H = 32, 24
+    pair = workloads.translation_pair(seed=11, width=W, height=H, shift=(3, -2), rects=0,
+                                      with_square=False)
+    img1, img2 = pair.img1, pair.img2
+    if C == 3:
+        rng = np.random.default_rng(5)
+        img1 = np.concatenate([img1, img1[:, :, ::-1], rng.permutation(img1.ravel()).reshape(img1.shape)])
+        img2 = np.concatenate([img2, img2[:, :, ::-1], np.zeros_like(img2)])
+        img2[2] = np.roll(np.roll(img1[2], -2, axis=0), 3, axis=1)   # same shift on channel 3
+        img2[1] = np.roll(np.roll(img1[1], -2, axis=0), 3, axis=1)
+    S = 2
+    P = O.Params(channels=C, scales=S, iters=4)
+    f1 = O.features_all(img1, S)
+    f2 = O.features_all(img2, S)
+    flow, cost, _ = O.match_features(P, f1, f2, W, H, 0, 0)
+    table = _exhaustive_table(f2[0], W, H)
+    checked = 0
+    for py in range(7, H - 7):
+        for px in range(7, W - 7):
+            E = _costs_at(table, f1[0], px, py)
+            zeros = np.argwhere(E == 0)
+            assert zeros.tolist() == [[8 * py - 16, 8 * px + 24]]
+            assert tuple(flow[py, px]) == (24, -16) and cost[py, px] == 0
+            checked += 1
+    assert checked >= 100
+
+
+@pytest.mark.parametrize("C,iters", [(1, 4), (3, 4), (1, 3), (3, 6)])
+def test_last_sweep_leaves_a_fixed_point_of_its_sources(C, iters):
+    # no random search follows the last sweep, so each final flow is the
+    # argmin over [current, vertical source, horizontal source] with the
+    # sources' final values, and on equal cost the later candidate
+    # (horizontal, then vertical) is the one kept (Sec. 3.1 Eq. 2, Sec. 4.5)
+    W, H = 28, 20
+    pair = workloads.layered_pair(seed=77 + C, width=W, height=H, channels=C, max_disp=5.0)
+    P = O.Params(channels=C, scales=2, iters=iters)
+    f1 = O.features_all(pair.img1, 2)
+    f2 = O.features_all(pair.img2, 2)
+    flow, cost, _ = O.match_features(P, f1, f2, W, H, 0, 1)
+    d = (iters - 1) % 4
+    dx = 1 if d in (0, 3) else -1
+    dy = 1 if d in (0, 2) else -1
+    table = _exhaustive_table(f2[0], W, H)
+    ties = 0
+    for py in range(H):
+        for px in range(W):
+            E = _costs_at(table, f1[0], px, py)
+            here = E[_flow_index(px, py, *flow[py, px])]
+            for sx, sy in ((px, py - dy), (px - dx, py)):          # vertical, horizontal
+                if not (0 <= sx < W and 0 <= sy < H):
+                    continue
+                cx, cy = O.clamp_flow(W, H, px, py, *map(int, flow[sy, sx]))
+                Ec = E[_flow_index(px, py, cx, cy)]
+                assert here <= Ec
+            hx, hy = px - dx, py
+            if 0 <= hx < W:
+                cx, cy = O.clamp_flow(W, H, px, py, *map(int, flow[hy, hx]))
+                if E[_flow_index(px, py, cx, cy)] == here:
+                    assert tuple(flow[py, px]) == (cx, cy)   # horizontal wins a tie
+                    ties += 1
+    assert ties > 0
+
+
+def _rerank_case(cands):
+    """Features for a 1-row frame: query pixel 0 is the zero vector; image 2
+    holds the given 9-d vectors from pixel 1 on, after a far vector at 0."""
+    W = len(cands) + 2
+    f1 = np.zeros((1, W, 9), np.int8)
+    f2 = np.full((1, W, 9), 60, np.int8)
+    f1[0, 1:] = 90
+    for i, c in enumerate(cands):
+        f2[0, 1 + i] = c
+    return f1, f2, W
+
+
+def test_rerank_takes_a_later_rank_with_lower_cost():
+    # Eq. 1: among the seeding candidates the one with the lowest matching
+    # error wins, even when it is not the nearest WHT vector
+    a = [1] * 9               # |a|^2 = 9,  sum|a| = 9
+    b = [3, 1] + [0] * 7      # |b|^2 = 10, sum|b| = 4
+    f1, f2, W = _rerank_case([a, b])
+    idx, dist = O.seed_knn(f1, f2, 1)
+    assert idx[0, 0, 0] == 1 and idx[0, 0, 1] == 2 and dist[0, 0, 0] < dist[0, 0, 1]
+    P = O.Params(channels=1, scales=1, iters=1)
+    flow, cost, _ = O.match_features(P, [f1], [f2], W, 1, 0, 0, until_level=0, until_sweeps=0)
+    assert tuple(flow[0, 0]) == (16, 0) and cost[0, 0] == 64 * 4
+
+
+def test_rerank_keeps_the_earlier_rank_on_equal_cost():
+    # equal matching errors: the nearer WHT vector (the earlier rank) stays,
+    # although the other candidate has the smaller pixel index
+    a = [2] + [0] * 8         # pixel 1: |a|^2 = 4, sum|a| = 2
+    b = [1, 1] + [0] * 7      # pixel 2: |b|^2 = 2, sum|b| = 2
+    f1, f2, W = _rerank_case([a, b])
+    idx, _ = O.seed_knn(f1, f2, 1)
+    assert idx[0, 0, 0] == 2 and idx[0, 0, 1] == 1
+    P = O.Params(channels=1, scales=1, iters=1)
+    flow, cost, _ = O.match_features(P, [f1], [f2], W, 1, 0, 0, until_level=0, until_sweeps=0)
+    assert tuple(flow[0, 0]) == (16, 0) and cost[0, 0] == 64 * 2
+
+
+def test_repetitive_object_needs_the_coarse_scale():
+    # Sec. 4.5: a repetitive pattern is matched flawlessly once the influence
+    # area of the coarsest scale is larger than the ambiguous pattern.  A 36 px
+    # object with a 12 px period moves on its own: 8 px windows (S = 1) match
+    # it at wrong period shifts, the 64 px windows of S = 4 see its outline.
+    cases = [(s, sh) for s in (5, 6, 7) for sh in ((11, 6), (-9, 5))]
+    exact = {1: 0, 4: 0}
+    wrong = {1: 0, 4: 0}
+    for seed, shift in cases:
+        pair = workloads.periodic_object_pair(seed=seed, shift=shift)
+        obj = np.all(pair.flow == shift, axis=2)
+        ys, xs = np.nonzero(obj)
+        core = np.zeros_like(obj)
+        core[ys.min() + 4:ys.max() - 3, xs.min() + 4:xs.max() - 3] = True
+        for S in (1, 4):
+            P = O.Params(channels=1, scales=S, iters=4)
+            flow, _, _ = O.match(P, pair.img1, pair.img2, 0, 0)
+            bad = np.any(flow != 8 * np.asarray(shift), axis=2) & core
+            exact[S] += int(not bad.any())
+            wrong[S] += int(bad.sum())
+    assert exact[1] == 0 and exact[4] >= 4
+    assert wrong[4] * 4 < wrong[1]

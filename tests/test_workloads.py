@@ -82,6 +82,21 @@ def test_periodic_pair_ground_truth():
     np.testing.assert_array_equal(pair.img1[:, :-12, :], pair.img1[:, 12:, :])
 
 
+@pytest.mark.parametrize("seed,shift", [(5, (11, 6)), (6, (-9, 5))])
+def test_periodic_object_pair_ground_truth(seed, shift):
+    pair = workloads.periodic_object_pair(seed=seed, shift=shift)
+    bad, vis = _constancy_violations(pair)
+    assert bad == 0 and vis > 0.8 * 95 * 95
+    obj = np.all(pair.flow == shift, axis=2)
+    assert obj.sum() == 36 * 36 and not pair.occ[obj].any()
+    # the object's texture repeats with its period inside the object
+    ys, xs = np.nonzero(obj)
+    y0, x0 = ys.min(), xs.min()
+    inner = pair.img1[0, y0:y0 + 36, x0:x0 + 36]
+    np.testing.assert_array_equal(inner[:, :-12], inner[:, 12:])
+    np.testing.assert_array_equal(inner[:-12, :], inner[12:, :])
+
+
 def test_layered_pair_motion_bounds():
     max_disp = 30.0
     pair = workloads.layered_pair(seed=8, width=160, height=96, channels=3, max_disp=max_disp)
