@@ -230,10 +230,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     side = torch.cuda.Stream(dev)
     side2 = torch.cuda.Stream(dev)
     ctx = ff.ff_create(cfg, local_rank, main)
-    if args.sweep_warps:
-        ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WARPS, args.sweep_warps)
-    if args.sweep_wpl:
-        ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_WPL, args.sweep_wpl)
+    if args.sweep_lanes:
+        ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_LANES, args.sweep_lanes)
     if args.seed_path == "mma":
         ff.ff_debug_set(ctx, ff.FF_DEBUG_SEED_TC, 0)
     img1 = torch.from_numpy(pair.img1).to(dev)
@@ -397,7 +395,7 @@ def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float
 
 
 def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int,
-                sweep_wpl: int = 0, autotune: bool = False) -> dict:
+                sweep_lanes: int = 0, autotune: bool = False) -> dict:
     """Throughput of the batched form on `pairs` (inputs resident, L2
     flushed between steps, one graph launch per step timed with CUDA events
     on the batch's stream)."""
@@ -423,10 +421,10 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
     if autotune:
         from paper_1703_02563_gb300 import autotune as at
         tuned = at.tune(cfg, descs, len(pairs), local_rank)
-        slots, sweep_wpl = tuned["slots"], tuned["wpl"]
+        slots, sweep_lanes = tuned["slots"], tuned["lanes"]
     b = ff.ff_batch_create(cfg, local_rank, slots=slots, stream=stream)
-    if sweep_wpl:
-        ff.ff_batch_debug_set(b, ff.FF_DEBUG_SWEEP_WPL, sweep_wpl)
+    if sweep_lanes:
+        ff.ff_batch_debug_set(b, ff.FF_DEBUG_SWEEP_LANES, sweep_lanes)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(warmup):
         ff.ff_batch_run(b, descs, use_graph=True)
@@ -582,12 +580,10 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="choose each batched leg's slots and sweep lane layout by timing "
                          "(autotune.py; the choice is cached)")
-    ap.add_argument("--sweep-warps", type=int, default=0,
-                    help="propagation warps per sweep CTA (1, 2, 4; 0 = library default)")
     ap.add_argument("--seed-path", choices=["tc", "mma"], default="tc",
                     help="seeding full pass on tcgen05 (default) or mma.sync")
-    ap.add_argument("--sweep-wpl", type=int, default=0,
-                    help="feature words per lane in the sweep (1, 2, 4; 0 = library default)")
+    ap.add_argument("--sweep-lanes", type=int, default=0,
+                    help="sweep lanes per grid point (2, 4; 0 = library default)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -666,7 +662,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world, local_rank)
     batched = {name: run_batched(pairs, prm, args.batch_slots, args.batch_steps, 3, local_rank,
-                                 args.sweep_wpl, args.autotune)
+                                 args.sweep_lanes, args.autotune)
                for name, (pairs, prm) in batches.items()}
     total_s, e2e_s = replica_times([res["total_ms"] / 1e3, res["e2e_s"]], world, "cuda")
     if rank != 0:

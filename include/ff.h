@@ -211,28 +211,30 @@ ff_status ff_get_features(ff_ctx *ctx, int slot, int level, int8_t *dst);
 ff_status ff_seed_knn(ff_ctx *ctx, ff_dir dir, int32_t *idx_out, int32_t *dist_out);
 
 /* Allocation-free seeding search.  The paper has no counterpart: this is an
- * interface for callers that cannot allocate device memory, for example code
- * that runs while a stream is being captured, a real-time loop that must not
- * wait on the allocator, or a host program that hands the library a fixed
- * memory budget and owns every allocation itself.  It computes what
- * ff_seed_knn computes, without a context, and allocates nothing: its
- * scratch (the per-chunk partial lists) is an 8 MiB array in the library's
- * static device memory, which every GPU that loads the library holds until
- * the process exits.
+ * interface for callers that cannot allocate device memory, for example a
+ * plug-in running inside a host application that owns every allocation and
+ * hands libraries a fixed budget, or a real-time loop that must never wait
+ * on the allocator (cudaMalloc and cudaFree can synchronise the device and
+ * stall every stream).  It computes what ff_seed_knn computes, without a
+ * context, and allocates nothing: its scratch (the per-chunk partial lists)
+ * is an 8 MiB array in the library's static device memory, which every GPU
+ * that loads the library holds until the process exits.
  *  feat_src0 / feat_dst0: level-0 features of the query and the candidate
  *    frame, int8 [h][w][P] (P = 16 for 1 channel, 32 for 3: the 9*channels
  *    codes of ff_get_features, then zero bytes), 16-byte aligned.
  *  idx_out / dist_out: int32 [H_c][W_c][leaf], as ff_seed_knn.
  *  cuda_stream: the stream to enqueue on (NULL = legacy default stream).
  *  why: NULL, or receives a static message when the call is rejected.
- * The first call on a device looks up the scratch's device address (with
- * that device current); make that first call before any stream capture.
- * Every call shares the scratch, which keeps the last call's contents, so
- * calls that overlap on a GPU race: order them on one stream.  Nothing in the
- * scratch needs clearing: each call writes every list it reads.  Returns
- * FF_EINVAL (nothing launched) for bad arguments, including more than 131072
- * coarsest-grid points, which is the scratch limit, and FF_ECUDA if the
- * set-up or a launch fails. */
+ * The first call on a device, and the first after that device's context was
+ * re-created, looks up the scratch's device address with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the scratch, which keeps the last call's contents, so calls that
+ * overlap on a GPU race: order them on one stream.  Nothing in the scratch
+ * needs clearing: each call writes every list it reads.  Returns FF_EINVAL
+ * (nothing launched) for bad arguments, including more than 131072
+ * coarsest-grid points, which is the scratch limit, and FF_ECUDA if a CUDA
+ * error from earlier work is still pending (nothing launched), if the
+ * set-up fails or if a launch fails. */
 ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, int w, int h,
                              int channels, int scales, int leaf, int stride, int32_t *idx_out,
                              int32_t *dist_out, void *cuda_stream, const char **why);
@@ -245,17 +247,16 @@ ff_status ff_sync(ff_ctx *ctx);
  * device-side wait (default 2 s).  FF_DEBUG_FORCE_TIMEOUT: when nonzero, the
  * next propagation sweeps wait for a boundary row that is never written, so
  * the bounded wait runs out and ff_sync reports FF_ETIMEOUT.
- * FF_DEBUG_SWEEP_WARPS: propagation warps per sweep CTA (1, 2 or 4; default
- * 1).  FF_DEBUG_SWEEP_WPL: feature words (4 dimensions each) per lane in the
- * sweep, 1, 2 or 4 (default 1 for gray, 2 for Lab); other than 2, one
- * propagation warp per CTA.  FF_DEBUG_SEED_TC: 1 (default) runs the seeding
+ * FF_DEBUG_SWEEP_LANES: lanes of the sweep's propagation warp per grid point,
+ * 4 (default: each candidate's cost split over two lanes, 8 rows per strip)
+ * or 2 (one lane per candidate, 16 rows per strip: fewer instructions per
+ * point, a longer step).  FF_DEBUG_SEED_TC: 1 (default) runs the seeding
  * search's full pass on the tcgen05 tensor cores, 0 on mma.sync.  Every value
  * gives the same results. */
 typedef enum {
     FF_DEBUG_WAIT_LIMIT_NS = 1,
     FF_DEBUG_FORCE_TIMEOUT = 2,
-    FF_DEBUG_SWEEP_WARPS = 3,
-    FF_DEBUG_SWEEP_WPL = 4,
+    FF_DEBUG_SWEEP_LANES = 4,
     FF_DEBUG_SEED_TC = 5
 } ff_debug_key;
 ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);

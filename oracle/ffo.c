@@ -463,10 +463,38 @@ void ffo_random_search_level(const int8_t *f1L, const int8_t *f2L, int C, int W,
     join_state(&st, (long)WL * HL, flow, cost);
 }
 
-int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *fdst,
-                       int W, int H, int dir, uint32_t pair_id, const int16_t *seeds_in,
-                       int until_level, int until_sweeps,
-                       int16_t *flow_out, int32_t *cost_out, int64_t *evals_out) {
+/* Eq. 1 / Eq. 4 at the coarsest scale: each of the l seeding candidates p2
+ * gives F = 8 (p2 - p); the one with the lowest E at scale N is kept, and on
+ * equal E the earlier rank (the nearer WHT vector) stays. */
+static void rerank(const ffo_params *prm, const int8_t *f1L, const int8_t *f2L, int W, int H,
+                   int L, const int32_t *knn_idx, state_t *cur, int64_t *evals) {
+    int n = 1 << L, WL, HL, C = prm->channels, l = prm->seed_leaf;
+    ffo_level_dims(W, H, L, &WL, &HL);
+    long NL = (long)WL * HL;
+    for (long i = 0; i < NL; i++) {
+        int gx = (int)(i % WL), gy = (int)(i / WL);
+        int px = gx * n, py = gy * n;
+        set_invalid(cur, i);
+        for (int r = 0; r < l; r++) {
+            int32_t idx = knn_idx[i * l + r];
+            if (idx < 0) break;
+            int32_t Fx = 8 * (idx % W - px), Fy = 8 * (idx / W - py);
+            ffo_clamp_flow(W, H, px, py, &Fx, &Fy);
+            int32_t E = ffo_cost(f1L, f2L, C, W, H, L, px, py, Fx, Fy);
+            (*evals)++;
+            if (E < cur->cost[i]) { /* ties: the earlier rank stays */
+                cur->fx[i] = (int16_t)Fx;
+                cur->fy[i] = (int16_t)Fy;
+                cur->cost[i] = E;
+            }
+        }
+    }
+}
+
+static int match_impl(const ffo_params *prm, const int8_t *fsrc, const int8_t *fdst,
+                      int W, int H, int dir, uint32_t pair_id, const int16_t *seeds_in,
+                      const int32_t *knn_in, int until_level, int until_sweeps,
+                      int16_t *flow_out, int32_t *cost_out, int64_t *evals_out) {
     int C = prm->channels, S = prm->scales, I = prm->iters, sch = prm->schedule;
     if (W < 1 || H < 1 || W > 4096 || H > 4096 || (C != 1 && C != 3) || S < 1 || S > 8 ||
         I < 1 || prm->seed_leaf < 1 || prm->seed_stride < 1 || prm->radius_q3 < 0 ||
@@ -502,30 +530,15 @@ int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *
                     cur.cost[i] = ffo_cost(f1L, f2L, C, W, H, L, gx * n, gy * n, Fx, Fy);
                     evals++;
                 }
+            } else if (knn_in) {
+                /* seeding lists computed beforehand (by ffo_seed_knn_rows) */
+                rerank(prm, f1L, f2L, W, H, L, knn_in, &cur, &evals);
             } else {
-                /* Eq. 1 / Eq. 4: the candidate with the lowest E at scale N */
                 int l = prm->seed_leaf;
                 int32_t *ki = (int32_t *)malloc(sizeof(int32_t) * NL * l);
                 int32_t *kd = (int32_t *)malloc(sizeof(int32_t) * NL * l);
                 ffo_seed_knn(fsrc, fdst, C, W, H, S, l, prm->seed_stride, ki, kd);
-                for (long i = 0; i < NL; i++) {
-                    int gx = (int)(i % WL), gy = (int)(i / WL);
-                    int px = gx * n, py = gy * n;
-                    set_invalid(&cur, i);
-                    for (int r = 0; r < l; r++) {
-                        int32_t idx = ki[i * l + r];
-                        if (idx < 0) break;
-                        int32_t Fx = 8 * (idx % W - px), Fy = 8 * (idx / W - py);
-                        ffo_clamp_flow(W, H, px, py, &Fx, &Fy);
-                        int32_t E = ffo_cost(f1L, f2L, C, W, H, L, px, py, Fx, Fy);
-                        evals++;
-                        if (E < cur.cost[i]) { /* ties: the earlier rank stays */
-                            cur.fx[i] = (int16_t)Fx;
-                            cur.fy[i] = (int16_t)Fy;
-                            cur.cost[i] = E;
-                        }
-                    }
-                }
+                rerank(prm, f1L, f2L, W, H, L, ki, &cur, &evals);
                 free(ki);
                 free(kd);
             }
@@ -573,6 +586,23 @@ int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *
     free(prev.cost);
     if (evals_out) *evals_out = evals;
     return 0;
+}
+
+int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *fdst,
+                       int W, int H, int dir, uint32_t pair_id, const int16_t *seeds_in,
+                       int until_level, int until_sweeps,
+                       int16_t *flow_out, int32_t *cost_out, int64_t *evals_out) {
+    return match_impl(prm, fsrc, fdst, W, H, dir, pair_id, seeds_in, NULL, until_level,
+                      until_sweeps, flow_out, cost_out, evals_out);
+}
+
+int ffo_match_features_knn(const ffo_params *prm, const int8_t *fsrc, const int8_t *fdst,
+                           int W, int H, int dir, uint32_t pair_id, const int32_t *knn_idx,
+                           int until_level, int until_sweeps,
+                           int16_t *flow_out, int32_t *cost_out, int64_t *evals_out) {
+    if (!knn_idx) return 1;
+    return match_impl(prm, fsrc, fdst, W, H, dir, pair_id, NULL, knn_idx, until_level,
+                      until_sweeps, flow_out, cost_out, evals_out);
 }
 
 int ffo_match(const ffo_params *prm, const uint8_t *src, const uint8_t *dst, int W, int H,

@@ -108,6 +108,14 @@ int ffo_match_features(const ffo_params *prm, const int8_t *fsrc, const int8_t *
                        int until_level, int until_sweeps,
                        int16_t *flow_out, int32_t *cost_out, int64_t *evals);
 
+/* the same with the seeding search's lists given: knn_idx [N_{S-1}][l] as
+ * ffo_seed_knn (or ffo_seed_knn_rows over all rows) writes them; the Eq. 1
+ * rerank and everything after it run here */
+int ffo_match_features_knn(const ffo_params *prm, const int8_t *fsrc, const int8_t *fdst,
+                           int W, int H, int dir, uint32_t pair_id, const int32_t *knn_idx,
+                           int until_level, int until_sweeps,
+                           int16_t *flow_out, int32_t *cost_out, int64_t *evals);
+
 /* same, computing the features of both images first */
 int ffo_match(const ffo_params *prm, const uint8_t *src, const uint8_t *dst, int W, int H,
               int dir, uint32_t pair_id, const int16_t *seeds_in,

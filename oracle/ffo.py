@@ -46,6 +46,8 @@ def lib():
         L.ffo_seed_knn_rows.restype = i
         L.ffo_match_features.argtypes = [P, P, P, i, i, i, ct.c_uint32, P, i, i, P, P, P]
         L.ffo_match_features.restype = i
+        L.ffo_match_features_knn.argtypes = [P, P, P, i, i, i, ct.c_uint32, P, i, i, P, P, P]
+        L.ffo_match_features_knn.restype = i
         L.ffo_match.argtypes = [P, P, P, i, i, i, ct.c_uint32, P, i, i, P, P, P]
         L.ffo_match.restype = i
         L.ffo_filter.argtypes = [P, P, i, i, i, P]
@@ -203,6 +205,58 @@ def seed_knn_rows(f1_0: np.ndarray, f2_0: np.ndarray, S: int, gy0: int, gy1: int
     lib().ffo_seed_knn_rows(_p(f1_0), _p(f2_0), D // 9, W, H, S, leaf, stride, gy0, gy1,
                             _p(idx), _p(dist))
     return idx, dist
+
+
+def seed_knn_threaded(f1_0: np.ndarray, f2_0: np.ndarray, S: int, leaf: int = 8,
+                      stride: int = 1, workers: int | None = None):
+    """ffo_seed_knn's lists, computed as independent bands of coarsest-grid
+    rows (ffo_seed_knn_rows) on a thread pool; ctypes releases the GIL during
+    each call.  The result is the same as seed_knn's: every row is computed
+    by the same sequential C code, only different rows run at once."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    f1_0 = np.ascontiguousarray(f1_0, np.int8)
+    f2_0 = np.ascontiguousarray(f2_0, np.int8)
+    H, W, D = f1_0.shape
+    WS, HS = level_dims(W, H, S - 1)
+    idx = np.full((HS, WS, leaf), -1, np.int32)
+    dist = np.full((HS, WS, leaf), -1, np.int32)
+    workers = workers or os.cpu_count() or 1
+    bands = [(y, y + 1) for y in range(HS)]
+
+    def run(band):
+        gy0, gy1 = band
+        bi = np.full((HS, WS, leaf), -1, np.int32)
+        bd = np.full((HS, WS, leaf), -1, np.int32)
+        lib().ffo_seed_knn_rows(_p(f1_0), _p(f2_0), D // 9, W, H, S, leaf, stride, gy0, gy1,
+                                _p(bi), _p(bd))
+        return gy0, gy1, bi[gy0:gy1], bd[gy0:gy1]
+
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        for gy0, gy1, bi, bd in ex.map(run, bands):
+            idx[gy0:gy1] = bi
+            dist[gy0:gy1] = bd
+    return idx, dist
+
+
+def match_features_knn(prm: Params, fsrc: list[np.ndarray], fdst: list[np.ndarray], W: int,
+                       H: int, direction: int, pair_id: int, knn_idx: np.ndarray):
+    """ffo_match_features with the seeding lists given (the Eq. 1 rerank and
+    everything after it run in the oracle).  Returns (flow, cost, evals)."""
+    Lf = prm.final_level()
+    WL, HL = level_dims(W, H, Lf)
+    flow = np.zeros((HL, WL, 2), np.int16)
+    cst = np.zeros((HL, WL), np.int32)
+    ev = ct.c_int64(0)
+    knn = np.ascontiguousarray(knn_idx, np.int32)
+    c = prm.c()
+    fs, fd = _flat_features(fsrc), _flat_features(fdst)
+    rc = lib().ffo_match_features_knn(ct.byref(c), _p(fs), _p(fd), W, H, direction, pair_id,
+                                      _p(knn), Lf, prm.sweeps(Lf), _p(flow), _p(cst),
+                                      ct.byref(ev))
+    if rc != 0:
+        raise ValueError("ffo_match_features_knn rejected its arguments")
+    return flow, cst, ev.value
 
 
 def match_features(prm: Params, fsrc: list[np.ndarray], fdst: list[np.ndarray], W: int, H: int,

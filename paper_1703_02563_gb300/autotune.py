@@ -1,7 +1,7 @@
 """Tuning of the batched form: matching-slot count and sweep lane layout.
 
 For a configuration and a sample batch (device inputs and outputs already
-allocated), times every candidate (slots, feature words per lane) through
+allocated), times every candidate (slots, sweep lanes per grid point) through
 ``ff_batch_run`` graphs with CUDA events and keeps the fastest in a JSON
 cache keyed by the device, channel count, scales, schedule and the batch's
 largest frame.  Every candidate computes the same results (the lane layout
@@ -25,9 +25,9 @@ def _key(cfg: ff.Config, device_name: str) -> str:
 
 
 def candidates(cfg: ff.Config, max_slots: int) -> list[tuple[int, int]]:
-    wpls = (2, 4) if cfg.channels == 3 else (1, 2)
+    lanes = (4, 2)
     slots = [s for s in (8, 16, 32, 48, 64) if s <= max_slots]
-    return [(s, w) for s in slots for w in wpls]
+    return [(s, w) for s in slots for w in lanes]
 
 
 def lookup(cfg: ff.Config, device: int = 0, path: str = DEFAULT_CACHE) -> dict | None:
@@ -42,14 +42,14 @@ def lookup(cfg: ff.Config, device: int = 0, path: str = DEFAULT_CACHE) -> dict |
 def tune(cfg: ff.Config, descs, n: int, device: int = 0, max_slots: int = 64, steps: int = 2,
          path: str | None = DEFAULT_CACHE) -> dict:
     """Times each candidate on the batch `descs` (n pairs); returns
-    {"slots", "wpl", "ms", "trials"} and stores it in the cache at `path`."""
+    {"slots", "lanes", "ms", "trials"} and stores it in the cache at `path`."""
     import torch
     stream = torch.cuda.Stream(device)
     trials = []
-    for slots, wpl in candidates(cfg, max_slots):
+    for slots, lanes in candidates(cfg, max_slots):
         b = ff.ff_batch_create(cfg, device, slots=slots, stream=stream)
         try:
-            ff.ff_batch_debug_set(b, ff.FF_DEBUG_SWEEP_WPL, wpl)
+            ff.ff_batch_debug_set(b, ff.FF_DEBUG_SWEEP_LANES, lanes)
             ff.ff_batch_run(b, descs, n, use_graph=True)      # capture + first run
             ff.ff_batch_sync(b)
             times = []
@@ -64,7 +64,7 @@ def tune(cfg: ff.Config, descs, n: int, device: int = 0, max_slots: int = 64, st
             ff.ff_batch_sync(b)
         finally:
             ff.ff_batch_destroy(b)
-        trials.append({"slots": slots, "wpl": wpl, "ms": min(times)})
+        trials.append({"slots": slots, "lanes": lanes, "ms": min(times)})
     best = min(trials, key=lambda t: t["ms"])
     result = dict(best, trials=trials)
     if path:

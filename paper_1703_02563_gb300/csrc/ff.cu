@@ -1,6 +1,7 @@
 // ff.cu - GB300 (sm_103a) kernels and C ABI of the Flow Fields
 // patch-matching loop (arXiv 1703.02563, Sec. 3).  The ABI is declared in
 // include/ff.h.
+#include <cuda.h>   // CUcontext / CUresult types only; the driver is reached through the runtime
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -569,8 +570,7 @@ struct ff_ctx {
     int *rf_parent = nullptr, *rf_size = nullptr;
     uint8_t *rf_flag = nullptr;
     unsigned long long wait_ns = 2000000000ull;
-    int sweep_warps = 1;   // propagation warps per sweep CTA: 1, 2 or 4
-    int sweep_wpl = 2;     // feature words per lane in the sweep: 1, 2 or 4 (set by ff_create)
+    int sweep_lanes = 4;   // propagation-warp lanes per grid point in the sweep: 2 or 4
     int seed_tc = 1;       // seeding full pass on tcgen05 (0: mma.sync)
     int force_timeout = 0;
     long long launches = 0;
@@ -670,15 +670,10 @@ size_t level_offset(int W, int H, int P, int L) {
     return off;
 }
 
-// rows per strip of the sweep kernel for `np` propagation warps per CTA
-// rows of one sweep strip for np propagation warps and wpl feature words
-// per lane; wpl = 1 gives the smallest strips
-int rows_per_strip(int C, int np, int wpl) {
-    int rw;
-    if (wpl == 1) rw = C == 1 ? SweepGeo<1, 1, 1>::RW : SweepGeo<3, 1, 1>::RW;
-    else if (wpl == 4) rw = C == 1 ? SweepGeo<1, 1, 4>::RW : SweepGeo<3, 1, 4>::RW;
-    else rw = C == 1 ? SweepGeo<1, 1, 2>::RW : SweepGeo<3, 1, 2>::RW;
-    return rw * np;
+// rows of one sweep strip for `lanes` propagation-warp lanes per grid point
+// (8 gives the smallest strips)
+int rows_per_strip(int lanes) {
+    return lanes == 2 ? SweepGeo<1, 1>::RW : (lanes == 8 ? SweepGeo<1, 4>::RW : SweepGeo<1, 2>::RW);
 }
 
 template <typename T>
@@ -939,48 +934,19 @@ ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L,
     a.epoch = 1u + (uint32_t)(L * kMaxIters + t);
     a.wait_ns = c->wait_ns;
     a.force_timeout = c->force_timeout;
-    const int R = rows_per_strip(c->C, c->sweep_warps, c->sweep_wpl);
+    const int R = rows_per_strip(c->sweep_lanes);
     const int nstrips = (HL + R - 1) / R;
     prof_begin(c, "k_sweep");
-#define FF_LAUNCH_SWEEP(CC, NPW, WPL) \
-    k_sweep<CC, NPW, WPL><<<nstrips, SweepGeo<CC, NPW, WPL>::THREADS, 0, c->stream>>>(a)
-    if (c->sweep_wpl != 2) {   // one propagation warp per strip
-        if (c->C == 1) {
-            // gray, one word per lane: the direction compiled in (measured 5%
-            // faster per pair; for Lab the same specialisation was 2% slower)
-            if (c->sweep_wpl == 1) {
-                switch (a.d) {
-                    case 0:
-                        k_sweep<1, 1, 1, 0>
-                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
-                        break;
-                    case 1:
-                        k_sweep<1, 1, 1, 1>
-                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
-                        break;
-                    case 2:
-                        k_sweep<1, 1, 1, 2>
-                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
-                        break;
-                    default:
-                        k_sweep<1, 1, 1, 3>
-                            <<<nstrips, SweepGeo<1, 1, 1>::THREADS, 0, c->stream>>>(a);
-                        break;
-                }
-            }
-            else FF_LAUNCH_SWEEP(1, 1, 4);
-        } else {
-            if (c->sweep_wpl == 1) FF_LAUNCH_SWEEP(3, 1, 1);
-            else FF_LAUNCH_SWEEP(3, 1, 4);
-        }
-    } else if (c->C == 1) {
-        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(1, 1, 2);
-        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(1, 2, 2);
-        else FF_LAUNCH_SWEEP(1, 4, 2);
+#define FF_LAUNCH_SWEEP(CC, LPC) \
+    k_sweep<CC, LPC><<<nstrips, SweepGeo<CC, LPC>::THREADS, 0, c->stream>>>(a)
+    if (c->C == 1) {
+        if (c->sweep_lanes == 2) FF_LAUNCH_SWEEP(1, 1);
+        else if (c->sweep_lanes == 8) FF_LAUNCH_SWEEP(1, 4);
+        else FF_LAUNCH_SWEEP(1, 2);
     } else {
-        if (c->sweep_warps == 1) FF_LAUNCH_SWEEP(3, 1, 2);
-        else if (c->sweep_warps == 2) FF_LAUNCH_SWEEP(3, 2, 2);
-        else FF_LAUNCH_SWEEP(3, 4, 2);
+        if (c->sweep_lanes == 2) FF_LAUNCH_SWEEP(3, 1);
+        else if (c->sweep_lanes == 8) FF_LAUNCH_SWEEP(3, 4);
+        else FF_LAUNCH_SWEEP(3, 2);
     }
 #undef FF_LAUNCH_SWEEP
     return check_launch(c, "k_sweep");
@@ -1215,21 +1181,77 @@ constexpr size_t kStaticScratchInt2 = (size_t)1 << 20;   // 8 MiB of int2
 static __device__ __align__(256) int2 g_seed_scratch[kStaticScratchInt2];
 
 // In host code g_seed_scratch names a host-side stand-in, not device memory:
-// the kernels get the device address, looked up once per device (with that
-// device current) and cached here.
+// the kernels get the device address from cudaGetSymbolAddress, called with
+// the device current.  The address is cached per CUDA context, keyed by the
+// context's process-unique id (cuCtxGetId), so a context that is torn down
+// and created again (cudaDeviceReset, a released primary context) gets a
+// fresh lookup instead of a stale address.  Where the driver does not offer
+// those entry points the address is looked up on every call.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+struct ScratchEntry {
+    int device;
+    unsigned long long ctx_id;
+    int2 *ptr;
+};
 std::mutex g_scratch_mutex;
-int2 *g_scratch_ptr[64] = {nullptr};
+ScratchEntry g_scratch_cache[64];
+int g_scratch_entries = 0;
+bool g_ctx_api_tried = false;
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
+void load_ctx_api() {
+    if (g_ctx_api_tried) return;
+    g_ctx_api_tried = true;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+        g_ctx_get_current = (PfnCtxGetCurrent)f1;
+        g_ctx_get_id = (PfnCtxGetId)f2;
+    }
+}
+
+// id of the calling thread's current context, 0 if there is none or it
+// cannot be read
+unsigned long long current_ctx_id() {
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 cudaError_t static_scratch(int device, int2 **out) {
-    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[device]) {
-        void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_seed_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[device] = (int2 *)ptr;
+    load_ctx_api();
+    const unsigned long long id = current_ctx_id();
+    if (id != 0)
+        for (int i = 0; i < g_scratch_entries; i++)
+            if (g_scratch_cache[i].device == device && g_scratch_cache[i].ctx_id == id) {
+                *out = g_scratch_cache[i].ptr;
+                return cudaSuccess;
+            }
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_seed_scratch);
+    if (e != cudaSuccess) return e;
+    *out = (int2 *)ptr;
+    // the lookup makes the device's primary context current if none was
+    const unsigned long long id2 = id != 0 ? id : current_ctx_id();
+    if (id2 != 0) {
+        int slot = -1;
+        for (int i = 0; i < g_scratch_entries; i++)
+            if (g_scratch_cache[i].device == device) slot = i;   // replaces a torn-down context's
+        if (slot < 0) slot = g_scratch_entries < 64 ? g_scratch_entries++ : device & 63;
+        g_scratch_cache[slot] = {device, id2, (int2 *)ptr};
     }
-    *out = g_scratch_ptr[device];
     return cudaSuccess;
 }
 
@@ -1281,9 +1303,7 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     c->stream = (cudaStream_t)cuda_stream;
     c->C = cfg->channels;
     c->P = cfg->channels == 1 ? 16 : 32;
-    // measured fastest per pair on GB300: 4 lanes of one word per gray point,
-    // 4 lanes of two words per Lab point
-    c->sweep_wpl = cfg->channels == 1 ? 1 : 2;
+    c->sweep_lanes = 4;   // the shortest step chain, for one pair at a time
     c->S = cfg->scales;
     c->I = cfg->iters;
     c->maxW = cfg->max_width;
@@ -1293,7 +1313,7 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     level_dims(c->maxW, c->maxH, c->S - 1, &WS, &HS);
     c->nq_cap = (size_t)WS * HS;
     const size_t npix = (size_t)c->maxW * c->maxH;
-    const int R = rows_per_strip(c->C, 1, 1);   // the smallest strip
+    const int R = rows_per_strip(8);   // the smallest strip
     c->edge_cap = (size_t)((c->maxH + R - 1) / R) * c->maxW;
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < 2 && e == cudaSuccess; s++) {
@@ -1588,6 +1608,10 @@ ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, i
     if (nq > max_slots)
         return *msg = "too many coarsest-grid points for the static scratch (limit 131072)",
                FF_EINVAL;
+    // an error left pending by earlier work on this thread is reported as
+    // such, not as this call's
+    if (cudaPeekAtLastError() != cudaSuccess)
+        return *msg = "a CUDA error from earlier work is pending; nothing launched", FF_ECUDA;
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     int2 *scratch = nullptr;
@@ -1612,10 +1636,10 @@ ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, i
     else
         k_seed_scan<3, kSeedQpt><<<grid, 128, 0, stream>>>(fs, fd, w, N, WS, (int)nq, stride, Wc,
                                                           ncand, chunk, scratch);
+    if (cudaGetLastError() != cudaSuccess) return *msg = "k_seed_scan launch failed", FF_ECUDA;
     k_seed_merge<<<(unsigned)((nq + 127) / 128), 128, 0, stream>>>(scratch, nchunks, (int)nq, leaf,
                                                                   idx_out, dist_out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return *msg = "kernel launch failed", FF_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return *msg = "k_seed_merge launch failed", FF_ECUDA;
     return FF_OK;
 }
 
@@ -1638,18 +1662,13 @@ ff_status ff_debug_set(ff_ctx *c, ff_debug_key key, long long value) {
         case FF_DEBUG_FORCE_TIMEOUT:
             c->force_timeout = value != 0;
             return FF_OK;
-        case FF_DEBUG_SWEEP_WARPS:
-            if (value != 1 && value != 2 && value != 4)
-                return fail(c, FF_EINVAL, "sweep warps must be 1, 2 or 4");
-            c->sweep_warps = (int)value;
-            return FF_OK;
         case FF_DEBUG_SEED_TC:
             c->seed_tc = value != 0;
             return FF_OK;
-        case FF_DEBUG_SWEEP_WPL:
-            if (value != 1 && value != 2 && value != 4)
-                return fail(c, FF_EINVAL, "sweep words per lane must be 1, 2 or 4");
-            c->sweep_wpl = (int)value;
+        case FF_DEBUG_SWEEP_LANES:
+            if (value != 2 && value != 4 && value != 8)
+                return fail(c, FF_EINVAL, "sweep lanes per grid point must be 2, 4 or 8");
+            c->sweep_lanes = (int)value;
             return FF_OK;
     }
     return fail(c, FF_EINVAL, "unknown debug key");
@@ -1826,10 +1845,6 @@ ff_status ff_batch_create(const ff_config *cfg, int device, int slots, void *cud
         ff_ctx *c = nullptr;
         s = ff_create(cfg, device, st, &c);
         if (s == FF_OK) {
-            // many pairs in flight: Lab sweeps with 2 lanes of 4 words per point
-            // (fewer warp instructions per point; measured 5% more pairs/s in a
-            // 32-pair batch, 14% fewer for one pair alone)
-            if (cfg->channels == 3) c->sweep_wpl = 4;
             b->slot.push_back(c);
         }
     }
@@ -2005,7 +2020,8 @@ size_t context_bytes(const ff_config &cfg) {
     int WS, HS;
     level_dims(cfg.max_width, cfg.max_height, cfg.scales - 1, &WS, &HS);
     const size_t nq = (size_t)WS * HS;
-    const int R = rows_per_strip(C, 1, 1);
+    (void)C;
+    const int R = rows_per_strip(8);
     const size_t edge = (size_t)((cfg.max_height + R - 1) / R) * cfg.max_width;
     size_t b = 2 * level_offset(cfg.max_width, cfg.max_height, P, cfg.scales);   // features
     b += 2 * npix * C + 3 * npix * 4 + npix;                                    // staging
@@ -2122,7 +2138,6 @@ ff_status ff_server_create(const ff_config *cfg, int device, size_t mem_budget, 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.err_host, kNumDirs * sizeof(int));
         if (e == cudaSuccess) s = ff_create(cfg, device, sl.stream, &sl.ctx);
-        if (s == FF_OK && sl.ctx && cfg->channels == 3) sl.ctx->sweep_wpl = 4;   // as in ff_batch
         if (e != cudaSuccess || s != FF_OK) break;
     }
     if (e != cudaSuccess || s != FF_OK) {

@@ -18,7 +18,7 @@ from . import _build
 FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_ETIMEOUT, FF_ESTATE = range(6)
 FF_FWD, FF_BWD, FF_BWD2 = 0, 1, 2
 FF_SCHED_BASIC, FF_SCHED_PLUS, FF_SCHED_PLUS_FAST, FF_SCHED_PLUS_FAST_X2 = 0, 1, 2, 3
-FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_WARPS, FF_DEBUG_SWEEP_WPL = 1, 2, 3, 4
+FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_LANES = 1, 2, 4
 FF_DEBUG_SEED_TC = 5
 INVALID = -32768
 

@@ -76,6 +76,43 @@ def test_batch_equals_oracle(schedule):
     ff.ff_batch_destroy(b)
 
 
+def test_batch_with_a_full_size_pair_equals_oracle():
+    # a 1242x375 pair (the KITTI size, Lab) in a batch with two small pairs,
+    # in the batch's own parameters (4 scales, 6 sweeps), as a replayed graph
+    from concurrent.futures import ThreadPoolExecutor
+    pairs = [workloads.batch_pair(5, 0, ((1242, 375),)), workloads.batch_pair(5, 1, ((97, 71),)),
+             workloads.batch_pair(5, 2, ((64, 48),))]
+    prm = workloads.BATCH_PARAMS
+    cfg = ff.Config(channels=3, scales=prm["scales"], iters=prm["iters"],
+                    radius_q3=prm["radius_q3"], max_width=1242, max_height=375)
+    b = ff.ff_batch_create(cfg, 0, slots=2)
+    imgs = _upload(pairs)
+    two_way = [False] * 3
+    outs = _outputs(pairs, cfg, two_way)
+    descs = ff.pair_descs(_descs(pairs, imgs, outs))
+    for _ in range(2):           # capture, then a replay
+        ff.ff_batch_run(b, descs, use_graph=True)
+        ff.ff_batch_sync(b)
+    P = O.Params(channels=3, scales=prm["scales"], iters=prm["iters"], radius_q3=prm["radius_q3"])
+    S = prm["scales"]
+    for k, (p, o) in enumerate(zip(pairs, outs)):
+        f1 = O.features_all(p.img1, S)
+        f2 = O.features_all(p.img2, S)
+        jobs = []
+        for d, (a, bb) in enumerate(((f1, f2), (f2, f1))):
+            ki, _ = O.seed_knn_threaded(a[0], bb[0], S)
+            jobs.append((a, bb, d, ki))
+        with ThreadPoolExecutor(max_workers=2) as ex:
+            (rf, _, _), (rb, _, _) = ex.map(
+                lambda j: O.match_features_knn(P, j[0], j[1], p.width, p.height, j[2], 100 + k,
+                                               j[3]), jobs)
+        np.testing.assert_array_equal(_host(o["fwd"]), rf, err_msg=f"pair {k}")
+        np.testing.assert_array_equal(_host(o["bwd"]), rb, err_msg=f"pair {k}")
+        np.testing.assert_array_equal(_host(o["mask"]), O.filter_mask(rf, rb, 8),
+                                      err_msg=f"pair {k}")
+    ff.ff_batch_destroy(b)
+
+
 def test_batch_same_alone_and_in_the_mix_and_graph_replays():
     import torch
     sizes = ((320, 240), (640, 480), (200, 150))
@@ -161,7 +198,7 @@ def test_autotune_times_every_candidate_and_keeps_the_fastest(tmp_path):
     cache = str(tmp_path / "tune.json")
     res = autotune.tune(cfg, descs, 4, max_slots=16, steps=1, path=cache)
     cands = autotune.candidates(cfg, 16)
-    assert [(t["slots"], t["wpl"]) for t in res["trials"]] == cands
+    assert [(t["slots"], t["lanes"]) for t in res["trials"]] == cands
     assert all(t["ms"] > 0 for t in res["trials"])
     assert res["ms"] == min(t["ms"] for t in res["trials"])
     assert autotune.lookup(cfg, 0, cache)["slots"] == res["slots"]

@@ -1,14 +1,16 @@
 """The allocation-free seeding search gives the same lists as ff_seed_knn.
 
-ff_seed_knn_static exists for callers that cannot allocate device memory
-(code running during stream capture, real-time loops that must not wait on
-the allocator, hosts that own every allocation); it keeps its scratch in the
-library's static device memory instead of a context.  This file is collected
-last so that a run stopping at the first failure has already run every other
-test; it also passes on its own in a fresh process.
+ff_seed_knn_static exists for callers that cannot allocate device memory: a
+plug-in inside a host program that owns every allocation and gives libraries
+a fixed budget, or a real-time loop that must never wait on the allocator
+(cudaMalloc and cudaFree can synchronise the device).  It keeps its scratch in
+the library's static device memory instead of a context.  This file is
+collected last so that a run stopping at the first failure has already run
+every other test; it also passes on its own in a fresh process.
 """
 from __future__ import annotations
 
+import numpy as np
 import pytest
 
 from paper_1703_02563_gb300 import ff, workloads
@@ -27,14 +29,15 @@ def _padded_level0(ctx, slot: int, channels: int):
     return out.contiguous()
 
 
-@pytest.mark.parametrize("name", ["sintel1024x436", "tiny128x96"])
-def test_static_seeding_equals_context_seeding_twice(name):
+@pytest.mark.parametrize("name,stride", [("sintel1024x436", 1), ("tiny128x96", 1),
+                                         ("tiny128x96", 2)])
+def test_static_seeding_equals_context_seeding_twice(name, stride):
     import torch
     pair, prm = workloads.make_workload(name)
     C, S = prm["channels"], prm["scales"]
     W, H = pair.width, pair.height
     cfg = ff.Config(channels=C, scales=S, iters=prm["iters"], radius_q3=prm["radius_q3"],
-                    max_width=W, max_height=H)
+                    max_width=W, max_height=H, seed_stride=stride)
     ctx = ff.Context(cfg)
     ctx.features(0, torch.from_numpy(pair.img1).cuda())
     ctx.features(1, torch.from_numpy(pair.img2).cuda())
@@ -51,6 +54,14 @@ def test_static_seeding_equals_context_seeding_twice(name):
             torch.cuda.synchronize()
             assert torch.equal(idx, ref_idx)
             assert torch.equal(dist, ref_dist)
+        if name == "tiny128x96":
+            # and both equal the oracle's exact search on the same features
+            import oracle as O
+            a = fs[..., :9 * C].cpu().numpy()
+            b = fd[..., :9 * C].cpu().numpy()
+            oi, od = O.seed_knn(a, b, S, cfg.seed_leaf, stride)
+            np.testing.assert_array_equal(idx.cpu().numpy().reshape(oi.shape), oi)
+            np.testing.assert_array_equal(dist.cpu().numpy().reshape(od.shape), od)
     ctx.close()
 
 
