@@ -15,14 +15,17 @@ instead of the basic schedule; ``--two-way`` adds the second backward flow
 and the two-way check of Sec. 3.7 to every step.
 
 ``--serve`` instead runs the serving loop (``ff_server_*``) on a Poisson
-stream of host-buffer requests of sizes 256x256 .. 1920x1080 (64-px steps),
-cut from full-HD layered pairs: capacity (all requests at once), then p50 /
-p99 latency at fractions of that rate.
+stream of host-buffer requests over independent layered pairs of sizes
+256x256 .. 1920x1080 (64-px steps): capacity (all requests at once), then
+p50 / p99 latency at fractions of that rate.
 
 The line's ``batched`` object times the batched form (``ff_batch_run``, one
 CUDA graph per step, pairs overlapping in matching slots) on two batches:
 32 Sintel-shaped pairs (distinct seeds) and 64 pairs of mixed sizes
-(320x240, 640x480, 1024x436, 1242x375).
+(320x240, 640x480, 1024x436, 1242x375).  Its ``serving`` object runs the
+serving loop on a shorter stream of the same kind (capacity and one Poisson
+load point at 0.8 of it).  ``roofline`` quotes the dominant kernel against
+ceilings measured on the running GPU (ff_measure_peaks).
 """
 from __future__ import annotations
 
@@ -151,8 +154,13 @@ def measured_peaks() -> dict:
 # ----------------------------------------------------------------------------
 # CPU oracle (the baseline and the reference arm)
 # ----------------------------------------------------------------------------
+# coarsest-grid query rows of the exact seeding search timed per direction in
+# one bounded oracle sample (the same for the CPU baseline and the reference arm)
+ORACLE_SEED_ROWS = 3
+
+
 def cpu_oracle_rate(pair, prm, schedule: int = 0, two_way: bool = False, region: int = 0,
-                    budget_rows: int = 6) -> dict:
+                    budget_rows: int = ORACLE_SEED_ROWS) -> dict:
     """Time the oracle, as it stands, on a bounded sample of one pair.
 
     Features of both frames, the full propagation of both directions (seeded
@@ -234,6 +242,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
         ff.ff_debug_set(ctx, ff.FF_DEBUG_SWEEP_LANES, args.sweep_lanes)
     if args.seed_path == "mma":
         ff.ff_debug_set(ctx, ff.FF_DEBUG_SEED_TC, 0)
+    peaks = ff.ff_measure_peaks(local_rank)
     img1 = torch.from_numpy(pair.img1).to(dev)
     img2 = torch.from_numpy(pair.img2).to(dev)
     flow_f = torch.empty((HL, WL, 2), dtype=torch.int16, device=dev)
@@ -343,12 +352,40 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     accuracy = flow_accuracy(flow_f.cpu().numpy(), mask.cpu().numpy(), pair, cfg.final_level())
     ff.ff_destroy(ctx)
     return {"total_ms": total_ms, "step_ms": step_ms, "kstats": kstats, "launches": launches,
+            "peaks": peaks,
             "accuracy": accuracy,
             "clocks": clocks, "e2e_s": e2e_s, "e2e_bytes": e2e_bytes, "W": W, "H": H, "C": C,
             "S": S, "I": I, "cfg": cfg, "prm": prm, "pair": pair, "workload": args.workload}
 
 
-ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12   # SMs x INT32 lanes/SM x max SM clock (Tops/s)
+# Algorithmic integer operations of the matching error per feature dimension:
+# the bilinear interpolation's 4 multiply-adds (2 ops each), the subtraction
+# of 64 q, the absolute value and the accumulation.
+OPS_PER_DIM = 11
+
+
+def sweep_diagonals(W: int, H: int, cfg) -> int:
+    """Anti-diagonals of every propagation sweep of one direction: the
+    sequential steps the raster order leaves (a point waits for its left and
+    upper neighbours), U_L + V_L - 1 per sweep of level L."""
+    n = 0
+    for L in range(cfg.scales):
+        wl, hl = level_dims(W, H, L)
+        n += cfg.sweeps(L) * (wl + hl - 1)
+    return n
+
+
+def step_floor_cycles(peaks: dict) -> float:
+    """Dependent latency of one wavefront step of the sweep, from measured
+    instruction latencies: the row above's decision arrives by a shuffle;
+    selecting and clamping the candidate (4 ALU), its tap address (9 ALU:
+    sign extension, rounding to the level, column and row offsets, 64-bit
+    address), one L1-hit load, the byte transpose (2 permutes), one dp4a,
+    absolute value and accumulation (3 ALU), the two-level shuffle exchange
+    of the costs (2 shuffles, 1 add) and the argmin over [current, vertical,
+    horizontal] into the next step's horizontal source (7 ALU)."""
+    return (3 * peaks["lat_shfl"] + peaks["lat_ldg_l1"] + 2 * peaks["lat_prmt"]
+            + peaks["lat_dp4a"] + 24 * peaks["lat_alu"])
 
 
 # ----------------------------------------------------------------------------
@@ -395,7 +432,7 @@ def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float
 
 
 def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int,
-                sweep_lanes: int = 0, autotune: bool = False) -> dict:
+                sweep_lanes: int = 0, autotune: bool = False, peak_tops: float | None = None) -> dict:
     """Throughput of the batched form on `pairs` (inputs resident, L2
     flushed between steps, one graph launch per step timed with CUDA events
     on the batch's stream)."""
@@ -447,27 +484,29 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
     total_s = sum(ms) / 1e3
     evals = sum(2 * eval_count(p.width, p.height, cfg) for p in pairs) * steps
     sweep_ops = sum(2 * sweep_evals(p.width, p.height, cfg) for p in pairs) * steps \
-        * 9 * prm["channels"] * 10
+        * 9 * prm["channels"] * OPS_PER_DIM
     return {"value": len(pairs) * steps / total_s, "unit": "pairs/s", "pairs": len(pairs),
             "slots": slots, "steps": steps, "ms_per_batch": total_s * 1e3 / steps,
             "evals_per_s": evals / total_s, "gpu_launches": launches,
-            # a lower bound on k_sweep's ALU fraction: all of the step's time charged to it
-            "sweep_alu_frac_of_step": sweep_ops / total_s / 1e12 / ALU_PEAK_TOPS,
+            # a lower bound on k_sweep's fraction of the measured per-dimension
+            # arithmetic peak: all of the step's time charged to the sweeps
+            "sweep_alu_frac_of_step": (sweep_ops / total_s / 1e12 / peak_tops)
+            if peak_tops else None,
             "sizes": sorted({f"{p.width}x{p.height}" for p in pairs}),
             **({"autotune": tuned} if tuned else {})}
 
 
-def recorded_traffic(kernel: str, workload: str) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on this workload and the kernel's sources are unchanged since."""
+def recorded_counters(kernel: str, workload: str) -> dict | None:
+    """Per-launch counters of a kernel from the committed ncu summary, if they
+    were taken on this workload and the kernel's sources are unchanged since."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", f"{kernel}_counters.json")) as f:
             rec = json.load(f)
         src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["sources"])
         if hashlib.sha256(src).hexdigest() != rec["source_sha256"] or rec["workload"] != workload:
             return None
-        return float(rec["traffic_bytes_per_launch"])
+        return rec
     except (OSError, KeyError, ValueError):
         return None
 
@@ -476,16 +515,21 @@ def roofline(res: dict, steps: int, n_dirs: int) -> dict:
     """Roofline of the kernel with the largest share of device time.
 
     k_sweep (propagation + random search) is integer-ALU work on a serial
-    wavefront.  Algorithmic work per evaluation: per feature dimension 4
-    multiply-adds of the bilinear taps, a subtraction, an absolute value and
-    an accumulation (7 int ops), plus 3 ops of tap/weight arithmetic
-    amortised per dimension = 10 int ops; evaluations per launch from
-    sweep_evals.  Peak: 152 SMs x 64 INT32 lanes x 2.07 GHz.
+    wavefront.  Its algorithmic work is OPS_PER_DIM integer operations per
+    feature dimension per evaluation (evaluations per launch from
+    sweep_evals); the peak is the same arithmetic's measured throughput
+    (ff_measure_peaks: sad_dims_per_s x OPS_PER_DIM), with the dp4a
+    instruction peak (8 ops per dp4a) beside it.  Its L2 fraction is the L2
+    traffic of one launch (ncu record) over the launch time, against the
+    measured L2 read bandwidth.  Its critical path is the cycles per
+    anti-diagonal (device time x SM clock over the sweeps' anti-diagonals)
+    against the dependent latency of one step (step_floor_cycles).
     k_seed_scan (the tensor-core seeding) is a dense contraction: 2 flops per
     multiply-add of (queries x candidates x K), against the measured bf16
     tensor peak.
     """
     ks = res["kstats"]
+    peaks = res["peaks"]
     tot = {k: v[1] for k, v in ks.items()}
     dom = max(tot, key=lambda k: tot[k])
     n_launch, ms = ks[dom]
@@ -493,14 +537,37 @@ def roofline(res: dict, steps: int, n_dirs: int) -> dict:
     share = ms / sum(tot.values())
     avg_ms = ms / max(n_launch, 1)
     if dom == "k_sweep":
-        ops_per_launch = n_dirs * steps * sweep_evals(W, H, res["cfg"]) * 9 * C * 10 / \
-            max(n_launch, 1)
-        achieved = ops_per_launch / (avg_ms / 1e3) / 1e12
-        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
-                "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
-                "traffic": recorded_traffic(dom, res["workload"]), "launches": n_launch,
-                "avg_launch_ms": avg_ms,
-                "share": share, "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2.07 GHz"}
+        dims = n_dirs * steps * sweep_evals(W, H, res["cfg"]) * 9 * C / max(n_launch, 1)
+        achieved = dims * OPS_PER_DIM / (avg_ms / 1e3) / 1e12
+        peak = peaks["sad_dims_per_s"] * OPS_PER_DIM / 1e12
+        dp4a_peak = peaks["dp4a_per_s"] * 8 / 1e12
+        rec = recorded_counters(dom, res["workload"])
+        l2 = None
+        traffic = None
+        if rec:
+            traffic = rec["dram_bytes_per_launch"]
+            l2_gbs = rec["l2_bytes_per_launch"] / (avg_ms / 1e3) / 1e9
+            l2 = {"achieved": l2_gbs, "peak": peaks["l2_read_gbs"], "unit": "GB/s",
+                  "frac": l2_gbs / peaks["l2_read_gbs"],
+                  "l2_bytes_per_launch": rec["l2_bytes_per_launch"],
+                  "source": "ncu lts__t_bytes.sum per launch (profiles/k_sweep_counters.json) "
+                            "over the live launch time; peak measured by ff_measure_peaks"}
+        clk = res["clocks"].get("sm_mhz") or 2070.0
+        diags = n_dirs * steps * sweep_diagonals(W, H, res["cfg"])
+        cyc = ms / 1e3 * clk * 1e6 / diags
+        floor = step_floor_cycles(peaks)
+        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
+                "launches": n_launch, "avg_launch_ms": avg_ms, "share": share,
+                "peak_source": "measured (ff_measure_peaks): the matching error's per-dimension "
+                               f"arithmetic at full occupancy, {OPS_PER_DIM} ops per dimension",
+                "dp4a_peak": dp4a_peak, "frac_of_dp4a_peak": achieved / dp4a_peak,
+                "l2": l2,
+                "critical_path": {"cycles_per_step": cyc, "floor_cycles": floor,
+                                  "frac": floor / cyc, "sm_mhz": clk,
+                                  "steps": "anti-diagonals U_L + V_L - 1 of every sweep",
+                                  "floor": "dependent latency of one step from measured "
+                                           "instruction latencies (step_floor_cycles)"}}
     if dom == "k_seed_scan":
         N = 1 << (S - 1)
         nq = ((W + N - 1) // N) * ((H + N - 1) // N)
@@ -513,43 +580,112 @@ def roofline(res: dict, steps: int, n_dirs: int) -> dict:
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "launches": n_launch, "avg_launch_ms": avg_ms, "share": share,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}
-    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": ALU_PEAK_TOPS,
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None,
             "unit": "Tops/s", "frac": None, "traffic": None, "launches": n_launch,
             "avg_launch_ms": avg_ms, "share": share}
 
 
-def run_serving(args, local_rank: int) -> dict:
-    """Capacity and latency of the serving loop (host buffers end to end)."""
+def _fp64_scalespace_wht(img: np.ndarray, L: int) -> np.ndarray:
+    """FP64 WHT of the scale-space image (the n x n block mean without
+    rounding, replicate border): separable +-1 sums over the 8 x 8 window at
+    offsets -3..+4, rows (u) then columns (v); [HL][WL][9C], dim c*9 + 3u + v."""
+    C, H, W = img.shape
+    n = 1 << L
+    WL, HL = -(-W // n), -(-H // n)
+    pad = np.pad(img.astype(np.float64), ((0, 0), (0, HL * n - H), (0, WL * n - W)), mode="edge")
+    D = np.pad(pad.reshape(C, HL, n, WL, n).mean(axis=(2, 4)), ((0, 0), (3, 4), (3, 4)),
+               mode="edge")
+    walsh = np.array([[1] * 8, [1] * 4 + [-1] * 4, [1, 1, -1, -1, -1, -1, 1, 1]], np.float64)
+    out = np.zeros((HL, WL, C, 3, 3))
+    for u in range(3):
+        rows = sum(walsh[u, i] * D[:, i:i + HL, :] for i in range(8))        # C, HL, WL+7
+        for v in range(3):
+            out[:, :, :, u, v] = np.moveaxis(
+                sum(walsh[v, j] * rows[:, :, j:j + WL] for j in range(8)), 0, -1)
+    return out.reshape(HL, WL, 9 * C)
+
+
+def precision_form(pair, scales: int, local_rank: int) -> dict:
+    """The precision form: the WHT of the FP32 scale-space image on the
+    tensor cores in bf16 and fp16 (FP32 accumulation) against FP64, per
+    level: max |coefficient error|, the bound the format's rounding allows,
+    and the int8 codes that differ from the FP64 coefficients' codes."""
+    import torch
+
+    from paper_1703_02563_gb300 import ff
+
+    C, H, W = pair.img1.shape
+    img = torch.from_numpy(pair.img1).cuda(local_rank)
+    half_ulp = {"bf16": 0.5, "fp16": 1.0 / 16.0}
+
+    def codes(c):
+        q = np.floor(c / 16.0 + 0.5)
+        q[..., 0::9] = np.floor(c[..., 0::9] / 64.0 + 0.5) - 128
+        return np.clip(q, -128, 127)
+
+    out = {}
+    for fmt in ("bf16", "fp16"):
+        levels = []
+        for L in range(scales):
+            WL, HL = level_dims(W, H, L)
+            t = torch.empty((HL, WL, 9 * C), dtype=torch.float32, device=img.device)
+            ff.ff_wht_coeffs_scalespace_tc(img, W, H, W, C, L, fmt == "fp16", t)
+            got = t.cpu().numpy().astype(np.float64)
+            ref = _fp64_scalespace_wht(pair.img1, L)
+            flips = int((codes(got) != codes(ref)).sum())
+            levels.append({"level": L, "max_abs_err": float(np.abs(got - ref).max()),
+                           "bound": 0.0 if L == 0 else 64 * half_ulp[fmt] + 64 * 2.0 ** -11,
+                           "int8_flips": flips, "codes": int(got.size)})
+        out[fmt] = {"levels": levels,
+                    "max_abs_err": max(x["max_abs_err"] for x in levels),
+                    "int8_flips": sum(x["int8_flips"] for x in levels),
+                    "codes": sum(x["codes"] for x in levels)}
+    out["note"] = ("FP32 scale-space image (area average without rounding) in bf16/fp16 on the "
+                   "tensor cores, FP32 accumulation, against an FP64 transform; matching uses "
+                   "the rounded integer level image and stays bit-exact")
+    return out
+
+
+def run_serving(pairs, reqs, fracs, budget_gb: float, region: int, local_rank: int) -> dict:
+    """Capacity and latency of the serving loop, host buffers end to end:
+    all requests submitted at once (capacity), then a Poisson stream at each
+    fraction of that rate; latency runs from a request's arrival to the poll
+    that retires it."""
     import torch
 
     from paper_1703_02563_gb300 import ff, serving, workloads
 
-    bases = args._serve_bases
     prm = workloads.BATCH_PARAMS
+    maxw = max(p.width for p in pairs)
+    maxh = max(p.height for p in pairs)
     cfg = ff.Config(channels=3, scales=prm["scales"], iters=prm["iters"],
-                    radius_q3=prm["radius_q3"], max_width=1920, max_height=1080,
-                    region_min=args.region)
+                    radius_q3=prm["radius_q3"], max_width=maxw, max_height=maxh,
+                    region_min=region)
     torch.cuda.set_device(local_rank)
-    srv = ff.ff_server_create(cfg, local_rank, mem_budget=int(args.serve_budget_gb * (1 << 30)),
+    srv = ff.ff_server_create(cfg, local_rank, mem_budget=int(budget_gb * (1 << 30)),
                               max_slots=256)
     slots = ff.ff_server_slots(srv)
-    frames = serving.HostFrames(bases)
-    pool = serving.OutputPool(slots + 64, 1920, 1080)
-    reqs = workloads.serving_requests(args.serve_requests, len(bases))
+    frames = serving.HostPairs(pairs)
+    pool = serving.OutputPool(slots + 64, maxw, maxh)
     sampler = ClockSampler(local_rank)
     serving.run(srv, frames, reqs[:2 * slots], None, pool)          # warm-up
     sampler.start()
     n0 = ff.ff_server_launch_count(srv)
     cap = serving.run(srv, frames, reqs, None, pool)
     points = []
-    for frac in args.serve_fracs:
+    for frac in fracs:
         points.append(dict(serving.run(srv, frames, reqs, frac * cap["pairs_per_s"], pool,
                                        seed=int(frac * 1000)), load=frac))
     launches = ff.ff_server_launch_count(srv) - n0
     clocks = sampler.stop()
     ff.ff_server_destroy(srv)
     return {"slots": slots, "slot_bytes": ff.ff_slot_bytes(cfg), "capacity": cap,
-            "latency": points, "clocks": clocks, "gpu_launches": launches}
+            "latency": points, "clocks": clocks, "gpu_launches": launches,
+            "pairs": len(pairs), "requests": len(reqs), "memory_budget_gb": budget_gb,
+            "sizes": "256..1920 x 256..1024 (and 1080) in 64-px steps, one per pair",
+            "generator": "independent layered pairs (Lab), displacement up to 300 px at "
+                         "1920 wide, scaled with the width; each request names a pair and "
+                         "carries its own random stream"}
 
 
 def main():
@@ -572,6 +708,10 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving loop on a Poisson request stream instead")
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-pairs", type=int, default=128,
+                    help="distinct layered pairs the --serve stream draws its requests from")
+    ap.add_argument("--serving-leg", type=int, default=480,
+                    help="requests of the default line's serving leg (0 = skip it)")
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--serve-fracs", type=float, nargs="*", default=[0.5, 0.8, 0.95])
     ap.add_argument("--batch-slots", type=int, default=32,
@@ -595,18 +735,23 @@ def main():
             return
         from paper_1703_02563_gb300 import workloads
         pair, prm = workloads.make_workload(args.workload)
+        sched = SCHEDULES[args.schedule]
+        # every step (warm-up included) times one bounded sample of the pair,
+        # the same sample cpu_baseline takes
         for _ in range(args.warmup):
-            pass
-        rates = []
+            cpu_oracle_rate(pair, prm, sched, args.two_way, args.region)
+        rates, walls = [], []
         sample = None
+        t_all = time.perf_counter()
         for _ in range(max(1, args.steps)):
-            r = cpu_oracle_rate(pair, prm, SCHEDULES[args.schedule], args.two_way, args.region,
-                                budget_rows=2)
+            r = cpu_oracle_rate(pair, prm, sched, args.two_way, args.region)
             rates.append(r["pairs_per_s"])
+            walls.append(r["wall_s"])
             sample = r["sample"]
+        wall = time.perf_counter() - t_all
         v = statistics.median(rates)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "n_gpus": args.gpus, "steps": len(rates), "warmup": args.warmup,
                 "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int8", "data": "synthetic",
                 "config": {"workload": args.workload, "frame": f"{pair.width}x{pair.height}",
@@ -614,6 +759,11 @@ def main():
                            "iters": prm["iters"], "radius_q3": prm["radius_q3"],
                            "schedule": args.schedule,
                            "backward_flows": 2 if args.two_way else 1},
+                "timing": {"samples_timed": len(rates), "sample_wall_s": statistics.mean(walls),
+                           "timed_wall_s": wall,
+                           "note": "each step is one bounded sample (wall time sample_wall_s); "
+                                   "ms_per_step is the time of a whole pair that the sample "
+                                   "extrapolates to (the seeding search scaled from its rows)"},
                 "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
@@ -625,19 +775,21 @@ def main():
         if rank != 0:
             return
         from paper_1703_02563_gb300 import workloads
-        args._serve_bases = workloads.serving_bases(4, workers=min(16, os.cpu_count() or 1))
-        res = run_serving(args, local_rank)
+        pairs = workloads.serving_pairs(args.serve_pairs, workers=min(16, os.cpu_count() or 1))
+        reqs = workloads.serving_pair_requests(args.serve_requests, len(pairs))
+        res = run_serving(pairs, reqs, args.serve_fracs, args.serve_budget_gb, args.region,
+                          local_rank)
         cap = res["capacity"]
         print(json.dumps({
             "metric": METRIC, "value": cap["pairs_per_s"], "unit": "pairs/s", "n_gpus": 1,
             "steps": cap["requests"], "warmup": 2 * res["slots"],
             "ms_per_step": 1e3 / cap["pairs_per_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": "serving: Poisson stream, 256x256..1920x1080 in 64-px steps, "
-                                   "crops of 4 full-HD layered pairs (flow up to 300 px)",
+            "config": {"workload": "serving: Poisson stream over independent layered pairs, "
+                                   "256x256..1920x1080 in 64-px steps (flow up to 300 px)",
                        "channels": 3, "scales": 4, "iters": 6, "radius_q3": 8,
                        "region_min": args.region, "slots": res["slots"],
-                       "slot_bytes": res["slot_bytes"],
+                       "slot_bytes": res["slot_bytes"], "pairs": res["pairs"],
                        "memory_budget_gb": args.serve_budget_gb,
                        "io": "host buffers: frames in, forward flow and mask out"},
             "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
@@ -656,14 +808,30 @@ def main():
             workloads.BATCH_PARAMS)
         batches["mixed64"] = (workloads.make_batch(64, seed=4, workers=workers),
                               workloads.BATCH_PARAMS)
+    serve_pairs = None
+    if args.serving_leg and args.schedule == "basic" and not args.two_way and world == 1:
+        from paper_1703_02563_gb300 import workloads
+        serve_pairs = workloads.serving_pairs(48, workers=min(16, os.cpu_count() or 1))
     if world > 1:
         import torch
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world, local_rank)
+    peak_tops = res["peaks"]["sad_dims_per_s"] * OPS_PER_DIM / 1e12
     batched = {name: run_batched(pairs, prm, args.batch_slots, args.batch_steps, 3, local_rank,
-                                 args.sweep_lanes, args.autotune)
+                                 args.sweep_lanes, args.autotune, peak_tops)
                for name, (pairs, prm) in batches.items()}
+    precision = None
+    if args.schedule == "basic" and not args.two_way and world == 1:
+        from paper_1703_02563_gb300 import workloads
+        kpair, kprm = workloads.make_workload("kitti1242x375")
+        precision = dict(precision_form(kpair, kprm["scales"], local_rank),
+                         workload="kitti1242x375")
+    serving_leg = None
+    if serve_pairs:
+        from paper_1703_02563_gb300 import workloads
+        reqs = workloads.serving_pair_requests(args.serving_leg, len(serve_pairs))
+        serving_leg = run_serving(serve_pairs, reqs, [0.8], args.serve_budget_gb, 0, local_rank)
     total_s, e2e_s = replica_times([res["total_ms"] / 1e3, res["e2e_s"]], world, "cuda")
     if rank != 0:
         if world > 1:
@@ -694,11 +862,19 @@ def main():
                 "h2d_bytes_per_step": res["e2e_bytes"][0],
                 "d2h_bytes_per_step": res["e2e_bytes"][1]},
         "roofline": roofline(res, K, n_dirs),
+        "peaks_measured": {k: (round(v, 3) if isinstance(v, float) else v)
+                           for k, v in res["peaks"].items()},
         "kernels_ms": {k: round(v[1], 4) for k, v in res["kstats"].items() if v[0]},
         "accuracy": res["accuracy"],
     }
     if batched:
         line["batched"] = batched
+    if precision:
+        line["precision"] = precision
+    if serving_leg:
+        line["serving"] = {k: serving_leg[k] for k in (
+            "capacity", "latency", "slots", "slot_bytes", "pairs", "requests",
+            "memory_budget_gb", "sizes", "generator", "gpu_launches", "clocks")}
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

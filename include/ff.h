@@ -200,6 +200,24 @@ ff_status ff_pair_host(ff_ctx *ctx, const uint8_t *img1_host, const uint8_t *img
 ff_status ff_wht_coeffs_tc(const uint8_t *img, int w, int h, int pitch, int channels, int level,
                            float *coeffs_out, void *cuda_stream);
 
+/* The precision form of the WHT: the transform of the FP32 scale-space
+ * image, i.e. level `level`'s n x n area average without rounding (Sec. 3.6,
+ * replicative border; exact in FP32), rounded to bf16 (fp16 = 0) or fp16
+ * (fp16 = 1) and multiplied with the +-1 Walsh basis on the tensor cores
+ * with FP32 accumulation.  coeffs_out float [H_L][W_L][9 * channels]
+ * (dimension ch*9 + 3u + v); img planar [channels][h][pitch] on the device.
+ * At level 0 the inputs are 8-bit integers, exact in both formats, so the
+ * result equals the exact transform; at level >= 1 each input is rounded to
+ * the nearest value of its format, at most half a unit in the last place
+ * (below 256: 0.5 for bf16, 1/16 for fp16), so a coefficient is within 64
+ * such half-units (32 and 4) plus the FP32 accumulation error of the FP64
+ * transform.  Matching never uses these values: ff_features quantises the
+ * rounded integer level image.  Stateless; enqueued on cuda_stream.  No
+ * paper counterpart: the paper's WHT is floating point on the CPU; this
+ * measures what the tensor-core formats lose against FP64. */
+ff_status ff_wht_coeffs_scalespace_tc(const uint8_t *img, int w, int h, int pitch, int channels,
+                                      int level, int fp16, float *coeffs_out, void *cuda_stream);
+
 /* Copies level `level` of slot `slot`'s features to dst: int8
  * [H_L][W_L][9 * channels] (dense, dimension index ch*9 + 3u + v). */
 ff_status ff_get_features(ff_ctx *ctx, int slot, int level, int8_t *dst);
@@ -238,6 +256,28 @@ ff_status ff_seed_knn(ff_ctx *ctx, ff_dir dir, int32_t *idx_out, int32_t *dist_o
 ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, int w, int h,
                              int channels, int scales, int leaf, int stride, int32_t *idx_out,
                              int32_t *dist_out, void *cuda_stream, const char **why);
+
+/* Ceilings of the running GPU, measured by microbenchmarks, for quoting the
+ * matching kernels against what this device can do (no counterpart in the
+ * paper, which reports CPU runtimes only).  Throughputs are whole-GPU rates
+ * at full occupancy: dp4a instructions (each 4 byte multiply-adds into an
+ * int32), three-input adds and 32-bit multiply-adds per second; the matching
+ * error's own arithmetic per feature dimension (byte transpose of the four
+ * bilinear taps, one dp4a forming the interpolation minus 64 q, absolute
+ * value, accumulation) in dimensions per second, from registers; and the
+ * read bandwidth of a 48 MB buffer resident in L2 (loads that skip L1).
+ * Latencies are SM clock cycles per instruction of a dependent chain run by
+ * one warp: integer add or xor, byte permute, dp4a, warp shuffle, shared load,
+ * global load hitting L1, global load hitting L2.  The call allocates its
+ * own buffers and stream, runs for a few tens of milliseconds and returns
+ * when done.  FF_EINVAL for a NULL out or a bad device, FF_ECUDA if a CUDA
+ * call fails. */
+typedef struct {
+    int sm_count;
+    double dp4a_per_s, iadd3_per_s, imad_per_s, sad_dims_per_s, l2_read_gbs;
+    double lat_alu, lat_prmt, lat_dp4a, lat_shfl, lat_lds, lat_ldg_l1, lat_ldg_l2;
+} ff_peaks;
+ff_status ff_measure_peaks(int device, ff_peaks *out);
 
 /* Blocks until the context's work is done; returns FF_ETIMEOUT if a bounded
  * device wait expired since the last ff_sync (and clears the record). */

@@ -10,7 +10,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = [os.path.join(CSRC, "ff.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("ff_kernels.cuh", "ff_sweep.cuh", "ff_seed.cuh",
-                                                  "ff_wht_tc.cuh", "ff_seed_tc.cuh")] \
+                                                  "ff_wht_tc.cuh", "ff_seed_tc.cuh",
+                                                  "ff_peaks.cuh")] \
     + [os.path.join(ROOT, "include", "ff.h")]
 LIB = os.path.join(HERE, "libff.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

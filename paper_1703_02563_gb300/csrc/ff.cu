@@ -327,6 +327,7 @@ __global__ void k_upsample(const uint32_t *__restrict__ pflow, int WP, const uin
 }
 
 #include "ff_sweep.cuh"
+#include "ff_peaks.cuh"
 #include "ff_seed.cuh"
 #include "ff_wht_tc.cuh"
 #include "ff_seed_tc.cuh"
@@ -570,7 +571,7 @@ struct ff_ctx {
     int *rf_parent = nullptr, *rf_size = nullptr;
     uint8_t *rf_flag = nullptr;
     unsigned long long wait_ns = 2000000000ull;
-    int sweep_lanes = 4;   // propagation-warp lanes per grid point in the sweep: 2 or 4
+    int sweep_lanes = 4;   // propagation-warp lanes per grid point in the sweep: 2, 4 or 8
     int seed_tc = 1;       // seeding full pass on tcgen05 (0: mma.sync)
     int force_timeout = 0;
     long long launches = 0;
@@ -1479,6 +1480,30 @@ ff_status ff_wht_coeffs_tc(const uint8_t *img, int w, int h, int pitch, int chan
     return cudaGetLastError() == cudaSuccess ? FF_OK : FF_ECUDA;
 }
 
+ff_status ff_wht_coeffs_scalespace_tc(const uint8_t *img, int w, int h, int pitch, int channels,
+                                      int level, int fp16, float *coeffs_out, void *cuda_stream) {
+    if (!img || !coeffs_out) return FF_EINVAL;
+    if (w < 1 || h < 1 || w > FF_MAX_DIM || h > FF_MAX_DIM || pitch < w) return FF_EINVAL;
+    if ((channels != 1 && channels != 3) || level < 0 || level >= FF_MAX_SCALES) return FF_EINVAL;
+    if (fp16 != 0 && fp16 != 1) return FF_EINVAL;
+    int WL, HL;
+    level_dims(w, h, level, &WL, &HL);
+    dim3 grid((WL + 15) / 16, (HL + 15) / 16);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+#define FF_LAUNCH_TCS(CC, IN) \
+    k_features_tc<CC, true, IN><<<grid, 128, 0, st>>>(img, pitch, w, h, level, WL, HL, nullptr, \
+                                                      coeffs_out)
+    if (channels == 1) {
+        if (fp16) FF_LAUNCH_TCS(1, 2);
+        else FF_LAUNCH_TCS(1, 1);
+    } else {
+        if (fp16) FF_LAUNCH_TCS(3, 2);
+        else FF_LAUNCH_TCS(3, 1);
+    }
+#undef FF_LAUNCH_TCS
+    return cudaGetLastError() == cudaSuccess ? FF_OK : FF_ECUDA;
+}
+
 ff_status ff_sparsify(ff_ctx *c, const int16_t *flow_fwd, const int16_t *flow_bwd1,
                       const int16_t *flow_bwd2, const uint8_t *mask_in, int q, int e,
                       uint8_t *mask_out) {
@@ -1641,6 +1666,98 @@ ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, i
                                                                   idx_out, dist_out);
     if (cudaGetLastError() != cudaSuccess) return *msg = "k_seed_merge launch failed", FF_ECUDA;
     return FF_OK;
+}
+
+ff_status ff_measure_peaks(int device, ff_peaks *out) {
+    if (!out) return FF_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return FF_EINVAL;
+    DeviceGuard guard(device);
+    memset(out, 0, sizeof(*out));
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return FF_ECUDA;
+    out->sm_count = sms;
+    const int blocks = sms * 8;                          // 2048 threads per SM
+    const size_t nthreads = (size_t)blocks * kPeakThreads;
+    const size_t l2_bytes = (size_t)48 << 20;            // resident in the L2
+    const uint32_t n_l1 = 1024, n_l2 = (uint32_t)(16u << 20) / 4;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    uint32_t *sink = nullptr, *chase1 = nullptr, *chase2 = nullptr;
+    uint4 *l2buf = nullptr;
+    double *lat = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sink, nthreads * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&l2buf, l2_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&chase1, n_l1 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&chase2, (size_t)n_l2 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&lat, 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(l2buf, 1, l2_bytes, st);
+    // times one launch (after an untimed one) in ms
+    auto timed = [&](auto launch) -> float {
+        float ms = 0.f;
+        launch();
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        launch();
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    if (e == cudaSuccess) {
+        const int it_int = 65536, it_sad = 8192;
+        const double n_int = (double)nthreads * it_int * kPeakChains;
+        const float t_dp4a = timed([&] { k_peak_int<0><<<blocks, kPeakThreads, 0, st>>>(sink, it_int, 7u); });
+        const float t_add = timed([&] { k_peak_int<1><<<blocks, kPeakThreads, 0, st>>>(sink, it_int, 7u); });
+        const float t_mad = timed([&] { k_peak_int<2><<<blocks, kPeakThreads, 0, st>>>(sink, it_int, 7u); });
+        const float t_sad = timed([&] { k_peak_sad<<<blocks, kPeakThreads, 0, st>>>(sink, it_sad, 7u); });
+        const int passes = 20;
+        const float t_l2 = timed([&] {
+            k_peak_l2<<<blocks, kPeakThreads, 0, st>>>(l2buf, l2_bytes / 16, passes, sink);
+        });
+        if (e == cudaSuccess) {
+            out->dp4a_per_s = n_int / (t_dp4a * 1e-3);
+            out->iadd3_per_s = n_int / (t_add * 1e-3);
+            out->imad_per_s = n_int / (t_mad * 1e-3);
+            out->sad_dims_per_s = (double)nthreads * it_sad * kPeakChains * 4 / (t_sad * 1e-3);
+            out->l2_read_gbs = (double)l2_bytes * passes / (t_l2 * 1e-3) / 1e9;
+        }
+    }
+    if (e == cudaSuccess) {
+        // latency chains: a 4 KB cycle for L1 hits, a 16 MB cycle (warmed into L2) for L2 hits
+        k_peak_chase_init<<<64, 256, 0, st>>>(chase1, n_l1, 33u);
+        k_peak_chase_init<<<sms * 4, 256, 0, st>>>(chase2, n_l2, 4099u);
+        k_peak_l2<<<blocks, kPeakThreads, 0, st>>>((const uint4 *)chase2, (size_t)n_l2 / 4, 2, sink);
+        k_peak_latency<<<1, 32, 0, st>>>(chase1, chase2, 4096, 7u, lat);
+        e = cudaGetLastError();
+        double h[16];
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, lat, 9 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            out->lat_alu = h[0];
+            out->lat_prmt = h[1];
+            out->lat_dp4a = h[2];
+            out->lat_shfl = h[3];
+            out->lat_lds = h[4];
+            out->lat_ldg_l1 = h[5];
+            out->lat_ldg_l2 = h[6];
+        }
+    }
+    cudaFree(lat);
+    cudaFree(chase2);
+    cudaFree(chase1);
+    cudaFree(l2buf);
+    cudaFree(sink);
+    if (e1) cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (st) cudaStreamDestroy(st);
+    return e == cudaSuccess ? FF_OK : FF_ECUDA;
 }
 
 ff_status ff_sync(ff_ctx *c) {
@@ -1845,6 +1962,9 @@ ff_status ff_batch_create(const ff_config *cfg, int device, int slots, void *cud
         ff_ctx *c = nullptr;
         s = ff_create(cfg, device, st, &c);
         if (s == FF_OK) {
+            // many pairs in flight: one lane per candidate (16 rows per strip,
+            // fewer instructions per grid point than the 4-lane layout)
+            c->sweep_lanes = 2;
             b->slot.push_back(c);
         }
     }
@@ -2138,6 +2258,7 @@ ff_status ff_server_create(const ff_config *cfg, int device, size_t mem_budget, 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.err_host, kNumDirs * sizeof(int));
         if (e == cudaSuccess) s = ff_create(cfg, device, sl.stream, &sl.ctx);
+        if (s == FF_OK && sl.ctx) sl.ctx->sweep_lanes = 2;   // as in ff_batch
         if (e != cudaSuccess || s != FF_OK) break;
     }
     if (e != cudaSuccess || s != FF_OK) {

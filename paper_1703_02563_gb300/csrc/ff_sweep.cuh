@@ -244,7 +244,7 @@ __device__ __forceinline__ bool wait_expired(unsigned long long &t0, unsigned lo
 template <int C, int LPC>
 __global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS) k_sweep(const SweepArgs a) {
     using SG = SweepGeo<C, LPC>;
-    constexpr int P = SG::P, G = SG::G, RW = SG::RW, NW = SG::NW;
+    constexpr int P = SG::P, G = SG::G, RW = SG::RW;
     constexpr int DI = SG::DI, DO = SG::DO, A = SG::A, LRING = SG::LRING;
     constexpr int WPC = SG::WPC, LWP = SG::LWP, WPH = SG::WPH, NB = SG::NB;
     constexpr int PD = SG::PD, PF_ROWS = SG::PF_ROWS, PF_COLS = SG::PF_COLS;

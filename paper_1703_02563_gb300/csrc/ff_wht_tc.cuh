@@ -7,9 +7,15 @@
 // sum of 64 such products is an integer of magnitude <= 16320 < 2^24, so the
 // FP32 accumulation is exact in any order and the coefficients equal the
 // integer ones.  The int8 codes are then quantised exactly as in k_features.
+//
+// The precision form (IN = 1, 2) feeds the FP32 scale-space image instead:
+// the level's area average without rounding (Sec. 3.6; exact in FP32, a sum
+// of at most 255 4^L < 2^24 divided by 4^L), rounded to bf16 (IN = 1) or
+// fp16 (IN = 2), and returns the FP32 coefficients.
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace ffk {
 
@@ -35,15 +41,31 @@ __device__ __forceinline__ int wht_basis(int k, int n) {
     return walsh8(n / 3, k >> 3) * walsh8(n % 3, k & 7);
 }
 
+// fp16 bits of a basis entry: +1, -1 or 0
+__device__ __forceinline__ uint16_t f16_sign(int v) {
+    return v > 0 ? (uint16_t)0x3C00 : (v < 0 ? (uint16_t)0xBC00 : (uint16_t)0);
+}
+
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                              uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // One CTA: a 16x16 tile of level pixels, 4 warps x 4 tile rows; each tile
 // row is one m16 fragment (16 pixels), K = 64 in 4 k-steps of two window
 // rows, N = 9 coefficients padded to 16 (two n8 fragments).
 // FLOAT_OUT: write the raw FP32 coefficients [HL][WL][9C] to fout instead
-// of the int8 features.
-template <int C, bool FLOAT_OUT>
+// of the int8 features.  IN: 0 the rounded integer level image in bf16; 1,
+// 2 the unrounded FP32 scale-space image rounded to bf16, fp16 (FLOAT_OUT).
+template <int C, bool FLOAT_OUT, int IN = 0>
 __global__ void __launch_bounds__(128)
     k_features_tc(const uint8_t *__restrict__ img, int pitch, int W, int H, int L, int WL, int HL,
                   uint8_t *__restrict__ out, float *__restrict__ fout) {
+    static_assert(IN == 0 || FLOAT_OUT, "the precision form returns coefficients");
     constexpr int TS = 16, TW = TS + 7, P = Geo<C>::P;
     __shared__ uint16_t sD[C][TW][TW + 1];                  // bf16 bits of D_n (tile + halo)
     __shared__ __align__(16) uint8_t sOut[TS * TS][P];     // int8 codes of the tile
@@ -61,7 +83,13 @@ __global__ void __launch_bounds__(128)
             const uint8_t *row = plane + (size_t)min(gy * n + i, H - 1) * pitch;
             for (int j = 0; j < n; j++) sum += row[min(gx * n + j, W - 1)];
         }
-        sD[c][ty][tx] = __bfloat16_as_ushort(__int2bfloat16_rn((sum + half) >> (2 * L)));
+        if constexpr (IN == 0) {
+            sD[c][ty][tx] = __bfloat16_as_ushort(__int2bfloat16_rn((sum + half) >> (2 * L)));
+        } else {
+            const float avg = (float)sum / (float)(n * n);   // exact
+            sD[c][ty][tx] = IN == 1 ? __bfloat16_as_ushort(__float2bfloat16_rn(avg))
+                                    : __half_as_ushort(__float2half_rn(avg));
+        }
     }
     if (!FLOAT_OUT)
         for (int k = threadIdx.x; k < TS * TS * P / 16; k += blockDim.x)
@@ -79,8 +107,12 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int r = 0; r < 2; r++) {
                 const int k0 = 8 * (2 * s + r) + 2 * t, col = 8 * nf + g;
-                bfr[s][nf][r] = bf16_pair(bf16_sign(wht_basis(k0, col)),
-                                          bf16_sign(wht_basis(k0 + 1, col)));
+                if constexpr (IN == 2)
+                    bfr[s][nf][r] = bf16_pair(f16_sign(wht_basis(k0, col)),
+                                              f16_sign(wht_basis(k0 + 1, col)));
+                else
+                    bfr[s][nf][r] = bf16_pair(bf16_sign(wht_basis(k0, col)),
+                                              bf16_sign(wht_basis(k0 + 1, col)));
             }
 #pragma unroll 1
     for (int rr = 0; rr < 4; rr++) {
@@ -98,8 +130,13 @@ __global__ void __launch_bounds__(128)
                 a[1] = bf16_pair(r0[g + 8 + 2 * t], r0[g + 8 + 2 * t + 1]);
                 a[2] = bf16_pair(r1[g + 2 * t], r1[g + 2 * t + 1]);
                 a[3] = bf16_pair(r1[g + 8 + 2 * t], r1[g + 8 + 2 * t + 1]);
-                mma_bf16_16816(acc[0], a, bfr[s][0][0], bfr[s][0][1]);
-                mma_bf16_16816(acc[1], a, bfr[s][1][0], bfr[s][1][1]);
+                if constexpr (IN == 2) {
+                    mma_f16_16816(acc[0], a, bfr[s][0][0], bfr[s][0][1]);
+                    mma_f16_16816(acc[1], a, bfr[s][1][0], bfr[s][1][1]);
+                } else {
+                    mma_bf16_16816(acc[0], a, bfr[s][0][0], bfr[s][0][1]);
+                    mma_bf16_16816(acc[1], a, bfr[s][1][0], bfr[s][1][1]);
+                }
             }
             // acc[nf][h * 2 + e]: pixel g + 8h, coefficient 8 nf + 2t + e
 #pragma unroll

@@ -24,8 +24,9 @@ INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
             "ff_match_until", "ff_filter", "ff_filter_2way", "ff_region_filter", "ff_sparsify", "ff_wht_coeffs_tc",
+            "ff_wht_coeffs_scalespace_tc",
             "ff_pair_host", "ff_get_features", "ff_seed_knn",
-            "ff_seed_knn_static", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
+            "ff_seed_knn_static", "ff_measure_peaks", "ff_sync", "ff_debug_set", "ff_profile", "ff_kernel_stats",
             "ff_launch_count", "ff_last_error", "ff_status_string", "ff_destroy",
             "ff_batch_create", "ff_batch_run", "ff_batch_set_stream", "ff_batch_sync",
             "ff_batch_debug_set",
@@ -57,6 +58,14 @@ class ff_host_pair(ct.Structure):
                 ("flow_bwd2", ct.c_void_p), ("mask", ct.c_void_p)]
 
 
+class ff_peaks(ct.Structure):
+    _fields_ = [("sm_count", ct.c_int), ("dp4a_per_s", ct.c_double), ("iadd3_per_s", ct.c_double),
+                ("imad_per_s", ct.c_double), ("sad_dims_per_s", ct.c_double),
+                ("l2_read_gbs", ct.c_double), ("lat_alu", ct.c_double), ("lat_prmt", ct.c_double),
+                ("lat_dp4a", ct.c_double), ("lat_shfl", ct.c_double), ("lat_lds", ct.c_double),
+                ("lat_ldg_l1", ct.c_double), ("lat_ldg_l2", ct.c_double)]
+
+
 class FFError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{status_string(status)}: {msg}")
@@ -84,11 +93,13 @@ def lib(build: bool = True) -> ct.CDLL:
         L.ff_region_filter.argtypes = [P, P, P, i, P]
         L.ff_sparsify.argtypes = [P, P, P, P, P, i, i, P]
         L.ff_wht_coeffs_tc.argtypes = [P, i, i, i, i, i, P, P]
+        L.ff_wht_coeffs_scalespace_tc.argtypes = [P, i, i, i, i, i, i, P, P]
         L.ff_pair_host.argtypes = [P, P, P, i, i, u32, P, P, P]
         L.ff_get_features.argtypes = [P, i, i, P]
         L.ff_seed_knn.argtypes = [P, i, P, P]
         L.ff_seed_knn_static.argtypes = [P, P, i, i, i, i, i, i, P, P, P,
                                          ct.POINTER(ct.c_char_p)]
+        L.ff_measure_peaks.argtypes = [i, ct.POINTER(ff_peaks)]
         L.ff_sync.argtypes = [P]
         L.ff_debug_set.argtypes = [P, i, ct.c_longlong]
         L.ff_profile.argtypes = [P, i]
@@ -266,6 +277,13 @@ def ff_sparsify(ctx: int, flow_fwd, flow_bwd1, flow_bwd2, mask_in, q: int, e: in
                                   _ptr(mask_in), q, e, _ptr(mask_out)))
 
 
+def ff_wht_coeffs_scalespace_tc(img, w: int, h: int, pitch: int, channels: int, level: int,
+                                fp16: bool, coeffs_out, stream=None) -> None:
+    """WHT of the FP32 scale-space image in bf16 or fp16 on the tensor cores."""
+    _check(None, lib().ff_wht_coeffs_scalespace_tc(_ptr(img), w, h, pitch, channels, level,
+                                                   int(fp16), _ptr(coeffs_out), _stream_handle(stream)))
+
+
 def ff_wht_coeffs_tc(img, w: int, h: int, pitch: int, channels: int, level: int, coeffs_out,
                      stream=None) -> None:
     _check(None, lib().ff_wht_coeffs_tc(_ptr(img), w, h, pitch, channels, level,
@@ -303,6 +321,16 @@ def ff_sync(ctx: int) -> None:
 
 def ff_debug_set(ctx: int, key: int, value: int) -> None:
     _check(ctx, lib().ff_debug_set(ctx, key, value))
+
+
+def ff_measure_peaks(device: int = 0) -> dict:
+    """The device's measured ceilings (see include/ff.h): a dict of the
+    ff_peaks fields."""
+    out = ff_peaks()
+    s = lib().ff_measure_peaks(device, ct.byref(out))
+    if s != FF_OK:
+        raise FFError(s, "ff_measure_peaks failed")
+    return {name: getattr(out, name) for name, _ in ff_peaks._fields_}
 
 
 def ff_profile(ctx: int, enable: bool) -> None:

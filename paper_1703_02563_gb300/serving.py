@@ -23,6 +23,9 @@ class HostFrames:
         self.frames = [(torch.from_numpy(np.ascontiguousarray(b.img1)).pin_memory(),
                         torch.from_numpy(np.ascontiguousarray(b.img2)).pin_memory()) for b in bases]
 
+    def pixels(self, r: dict) -> int:
+        return r["w"] * r["h"]
+
     def request(self, r: dict, two_way: bool, out: dict | None) -> ff.ff_host_pair:
         i1, i2 = self.frames[r["base"]]
         C, H, W = i1.shape
@@ -32,6 +35,27 @@ class HostFrames:
                                r["pair_id"], int(two_way), ff._ptr(out.get("fwd")),
                                ff._ptr(out.get("bwd")), ff._ptr(out.get("bwd2")),
                                ff._ptr(out.get("mask")))
+
+
+class HostPairs:
+    """Pinned copies of independent pairs; a request names one of them."""
+
+    def __init__(self, pairs):
+        import torch
+        self.frames = [(torch.from_numpy(np.ascontiguousarray(p.img1)).pin_memory(),
+                        torch.from_numpy(np.ascontiguousarray(p.img2)).pin_memory()) for p in pairs]
+
+    def request(self, r: dict, two_way: bool, out: dict | None) -> ff.ff_host_pair:
+        i1, i2 = self.frames[r["pair"]]
+        C, H, W = i1.shape
+        out = out or {}
+        return ff.ff_host_pair(i1.data_ptr(), i2.data_ptr(), W, H, W, H * W, r["pair_id"],
+                               int(two_way), ff._ptr(out.get("fwd")), ff._ptr(out.get("bwd")),
+                               ff._ptr(out.get("bwd2")), ff._ptr(out.get("mask")))
+
+    def pixels(self, r: dict) -> int:
+        _, H, W = self.frames[r["pair"]][0].shape
+        return W * H
 
 
 class OutputPool:
@@ -79,7 +103,7 @@ def run(srv: int, frames: HostFrames, reqs: list[dict], rate: float | None, pool
             first_done = now if first_done is None else first_done
             last_done = now
     span = last_done - (arrival[0] if rate is not None else 0.0)
-    pixels = sum(r["w"] * r["h"] for r in reqs)
+    pixels = sum(frames.pixels(r) for r in reqs)
     return {"requests": n, "rate_per_s": rate, "pairs_per_s": n / span,
             "mpix_per_s": pixels / span / 1e6,
             "p50_ms": float(np.percentile(lat, 50) * 1e3),

@@ -586,6 +586,34 @@ SERVE_WIDTHS = tuple(range(256, 1921, 64))
 SERVE_HEIGHTS = tuple(range(256, 1025, 64)) + (1080,)
 
 
+def _serving_pair(a) -> FramePair:
+    seed, w, h = a
+    return layered_pair(seed=seed, width=w, height=h, channels=3, max_disp=300.0 * w / 1920.0)
+
+
+def serving_pairs(n: int, seed: int = 8, workers: int = 0, widths=SERVE_WIDTHS,
+                  heights=SERVE_HEIGHTS) -> list[FramePair]:
+    """n independent layered pairs (the Sintel-shaped generator, Lab), each
+    with its own size drawn uniformly from widths x heights, its own layers
+    and motions, displacements up to 300 px at 1920 wide (scaled with the
+    width); `workers` > 1 generates them in a 'spawn' process pool."""
+    rng = np.random.default_rng(seed)
+    args = [(seed * 100000 + k, int(widths[int(rng.integers(0, len(widths)))]),
+             int(heights[int(rng.integers(0, len(heights)))])) for k in range(n)]
+    if workers > 1 and n > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, n)) as pool:
+            return pool.map(_serving_pair, args)
+    return [_serving_pair(a) for a in args]
+
+
+def serving_pair_requests(n: int, n_pairs: int, seed: int = 9) -> list[dict]:
+    """n requests over n_pairs pairs: each names a pair drawn uniformly and
+    carries its own pair id (its own random-search stream)."""
+    rng = np.random.default_rng(seed)
+    return [dict(pair=int(rng.integers(0, n_pairs)), pair_id=k) for k in range(n)]
+
+
 def _serving_base(seed: int) -> FramePair:
     return layered_pair(seed=seed, width=1920, height=1080, channels=3, max_disp=300.0)
 

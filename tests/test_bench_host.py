@@ -41,18 +41,30 @@ def test_sweep_roofline_arithmetic():
     # one direction's sweeps on a 64x48 frame, timed as 10 launches of 2 ms
     cfg = ff.Config(channels=3, scales=2, iters=5)
     W, H = 64, 48
+    peaks = {"sad_dims_per_s": 5e12, "dp4a_per_s": 2e13, "l2_read_gbs": 2e4,
+             "lat_shfl": 20.0, "lat_ldg_l1": 40.0, "lat_prmt": 5.0, "lat_dp4a": 6.0,
+             "lat_alu": 4.0}
     res = {"kstats": {"k_sweep": (10, 20.0), "k_features": (2, 0.5)},
-           "W": W, "H": H, "C": 3, "S": 2, "I": 5, "cfg": cfg, "workload": "none"}
+           "W": W, "H": H, "C": 3, "S": 2, "I": 5, "cfg": cfg, "workload": "none",
+           "peaks": peaks, "clocks": {"sm_mhz": 2000.0}}
     r = bench.roofline(res, steps=1, n_dirs=1)
     evals = bench.sweep_evals(W, H, cfg)
     # by hand: level 0 64x48, level 1 32x24; 5 sweeps (2 candidates per point, one
     # fewer per incoming border point) and 4 random searches per level
     by_hand = sum(5 * (2 * w * h - w - h) + 4 * w * h for w, h in ((64, 48), (32, 24)))
     assert evals == by_hand
-    ops_per_launch = evals * 27 * 10 / 10
+    # 27 dimensions, 11 operations each (4 multiply-adds, subtract, abs, add)
+    ops_per_launch = evals * 27 * 11 / 10
     assert r["kernel"] == "k_sweep" and r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(ops_per_launch / 2e-3 / 1e12)
+    assert r["peak"] == pytest.approx(5e12 * 11 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["frac_of_dp4a_peak"] == pytest.approx(r["achieved"] / (2e13 * 8 / 1e12))
     assert r["share"] == pytest.approx(20.0 / 20.5)
-    assert r["traffic"] is None          # no recorded capture for this workload
-    assert r["peak"] == pytest.approx(152 * 64 * 2.07e9 / 1e12)
+    assert r["traffic"] is None and r["l2"] is None   # no recorded capture for this workload
+    # critical path: 5 sweeps per level of (64 + 48 - 1) and (32 + 24 - 1) anti-diagonals
+    diags = 5 * (64 + 48 - 1) + 5 * (32 + 24 - 1)
+    cp = r["critical_path"]
+    assert cp["cycles_per_step"] == pytest.approx(20.0e-3 * 2000e6 / diags)
+    assert cp["floor_cycles"] == pytest.approx(3 * 20 + 40 + 2 * 5 + 6 + 24 * 4)
+    assert cp["frac"] == pytest.approx(cp["floor_cycles"] / cp["cycles_per_step"])

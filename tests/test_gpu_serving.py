@@ -2,6 +2,8 @@
 device; every result equals the same pair matched alone (and the oracle)."""
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import pytest
 
@@ -83,6 +85,43 @@ def test_open_loop_run_retires_every_request():
     assert res["p99_ms"] >= res["p50_ms"] > 0
     assert len(pool.free) == 6
     ff.ff_server_destroy(srv)
+
+
+def test_independent_pairs_served_equal_the_pairs_alone():
+    # the benchmark's stream: independent pairs of their own sizes, each
+    # request naming one pair with its own random stream
+    import torch
+    pairs = workloads.serving_pairs(4, seed=12, widths=(64, 128, 192), heights=(64, 96, 128))
+    reqs = workloads.serving_pair_requests(10, len(pairs), seed=2)
+    maxw = max(p.width for p in pairs)
+    maxh = max(p.height for p in pairs)
+    cfg = ff.Config(channels=3, scales=3, iters=4, max_width=maxw, max_height=maxh)
+    srv = ff.ff_server_create(cfg, 0, mem_budget=3 * ff.ff_slot_bytes(cfg), max_slots=3)
+    frames = serving.HostPairs(pairs)
+    pool = serving.OutputPool(len(reqs), maxw, maxh)
+    outs = list(pool.free)
+    res = serving.run(srv, frames, reqs, None, pool, timeout_s=120)
+    assert res["requests"] == len(reqs) and res["failures"] == 0
+    assert res["mpix_per_s"] > 0
+    ff.ff_server_destroy(srv)
+    # every buffer came back; which buffer served which request is the pool's
+    # business, so check each request alone against the oracle instead
+    P = O.Params(channels=3, scales=3, iters=4)
+    srv = ff.ff_server_create(cfg, 0, mem_budget=3 * ff.ff_slot_bytes(cfg), max_slots=3)
+    for r in reqs[:4]:
+        p = pairs[r["pair"]]
+        out = dict(fwd=torch.full((p.height * p.width * 2,), 3, dtype=torch.int16).pin_memory(),
+                   mask=torch.full((p.height * p.width,), 3, dtype=torch.uint8).pin_memory())
+        t = ff.ff_server_submit(srv, frames.request(r, False, out))
+        done = []
+        t0 = time.perf_counter()
+        while not done and time.perf_counter() - t0 < 60:
+            done = ff.ff_server_poll(srv)
+        assert done == [(t, ff.FF_OK)]
+        rf, _, _ = O.match(P, p.img1, p.img2, 0, r["pair_id"])
+        np.testing.assert_array_equal(out["fwd"].numpy().reshape(rf.shape), rf)
+    ff.ff_server_destroy(srv)
+    assert len(outs) == len(reqs)
 
 
 def test_slot_bytes_match_what_a_context_allocates():
