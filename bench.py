@@ -714,7 +714,7 @@ def main():
                     help="requests of the default line's serving leg (0 = skip it)")
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--serve-fracs", type=float, nargs="*", default=[0.5, 0.8, 0.95])
-    ap.add_argument("--batch-slots", type=int, default=32,
+    ap.add_argument("--batch-slots", type=int, default=64,
                     help="matching slots of the batched legs (0 = skip them)")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--autotune", action="store_true",

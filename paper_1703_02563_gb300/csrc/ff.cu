@@ -941,11 +941,13 @@ ff_status launch_sweep(ff_ctx *c, int d, const uint8_t *f1L, const uint8_t *f2L,
 #define FF_LAUNCH_SWEEP(CC, LPC) \
     k_sweep<CC, LPC><<<nstrips, SweepGeo<CC, LPC>::THREADS, 0, c->stream>>>(a)
     if (c->C == 1) {
-        if (c->sweep_lanes == 2) FF_LAUNCH_SWEEP(1, 1);
+        if (c->sweep_lanes == 2)
+            k_sweep_many<1><<<nstrips, SweepGeo<1, 1>::THREADS, 0, c->stream>>>(a);
         else if (c->sweep_lanes == 8) FF_LAUNCH_SWEEP(1, 4);
         else FF_LAUNCH_SWEEP(1, 2);
     } else {
-        if (c->sweep_lanes == 2) FF_LAUNCH_SWEEP(3, 1);
+        if (c->sweep_lanes == 2)
+            k_sweep_many<3><<<nstrips, SweepGeo<3, 1>::THREADS, 0, c->stream>>>(a);
         else if (c->sweep_lanes == 8) FF_LAUNCH_SWEEP(3, 4);
         else FF_LAUNCH_SWEEP(3, 2);
     }

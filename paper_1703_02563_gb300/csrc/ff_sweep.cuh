@@ -23,7 +23,10 @@ struct SweepArgs {
 // Geometry of a sweep CTA.  A CTA owns a strip of RW rows and has five warps:
 // propagation (warp 0), random search (1), input stager (2), L1 warmer (3)
 // and boundary-row loader (4), so the propagation warp shares its SM
-// sub-partition only with the loader, which mostly sleeps.
+// sub-partition only with the loader, which mostly sleeps.  The layout for
+// many pairs in flight (LPC = 1) has no warmer (the loader is warp 3): with
+// several CTAs per SM the warming copies cost more issue slots than the L1
+// hits they buy (measured on the 32- and 64-pair batches).
 //
 // A grid point is handled by G = 2 LPC lanes of the propagation warp: lanes
 // 0..LPC-1 evaluate the vertical candidate, lanes LPC..2 LPC-1 the horizontal
@@ -43,15 +46,21 @@ template <int C, int LPC> struct SweepGeo {
     static constexpr int HL_ = NW / WPH;             // random-search lanes holding words
     static constexpr int QB = P / G >= 4 ? P / G : 4;  // query bytes a stager lane copies
     static constexpr int QL = P / QB;                // stager lanes holding query bytes
-    static constexpr int DI = 16;                    // staged-input ring depth (steps)
+    // One lane per candidate is the layout for many pairs in flight: a
+    // shorter input ring (8 steps, staged 4 ahead) and a register bound let
+    // six CTAs share an SM, whose other CTAs hide the staging latency.
+    static constexpr int DI = LPC == 1 ? 8 : 16;     // staged-input ring depth (steps)
     static constexpr int DO = 16;                    // result ring depth (steps)
-    static constexpr int A = 8;                      // staging distance (steps ahead)
+    static constexpr int A = LPC == 1 ? 4 : 8;       // staging distance (steps ahead)
+    static constexpr int MIN_CTAS = 8;               // CTAs per SM the registers allow (LPC 1)
+    static constexpr bool WARM = LPC != 1;           // an L1-warming warp
+    static constexpr int LOADER = WARM ? 4 : 3;      // the loader's warp
     static constexpr int LRING = 128;                // previous strip -> this strip ring
     static constexpr int NB = 8 / G;                 // random-search offsets per lane per 8 steps
     static constexpr int PD = 1;                     // L1 warming distance (level pixels)
     static constexpr int PF_COLS = 4;                // feature columns warmed from the target on
     static constexpr int PF_ROWS = LPC == 2 ? 6 : 4; // feature rows warmed around the target
-    static constexpr int THREADS = 5 * 32;
+    static constexpr int THREADS = (WARM ? 5 : 4) * 32;
 };
 
 template <int C, int LPC> struct SweepShared {
@@ -242,7 +251,7 @@ __device__ __forceinline__ bool wait_expired(unsigned long long &t0, unsigned lo
 // raises the CTA's abort flag and returns; every other wait in the CTA
 // checks that flag on its slow path.
 template <int C, int LPC>
-__global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS) k_sweep(const SweepArgs a) {
+__device__ __forceinline__ void sweep_body(const SweepArgs &a) {
     using SG = SweepGeo<C, LPC>;
     constexpr int P = SG::P, G = SG::G, RW = SG::RW;
     constexpr int DI = SG::DI, DO = SG::DO, A = SG::A, LRING = SG::LRING;
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS) k_sweep(const Sweep
     const int v0 = strip * RW;
     const int warp = tid >> 5, lane = tid & 31;
 
-    if (warp == 4) {
+    if (warp == SG::LOADER) {
         // ---------------- loader warp: previous strip's last row -> lring
         if (strip == 0) return;
         const unsigned long long *src = a.edge + (size_t)(strip - 1) * U;
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS) k_sweep(const Sweep
     const uint8_t *f1L = a.f1L, *f2L = a.f2L;
     const size_t rowbase = (size_t)gy * U;
 
-    if (warp == 3) {
+    if (SG::WARM && warp == 3) {
         // ================= warming warp =================
         // Warms L1 with the feature sectors the propagation warp will read two
         // points after each decision: rows iy-2 .. iy+3 around the target of
@@ -613,6 +622,19 @@ __global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS) k_sweep(const Sweep
         }
         if (g == 0) sts64(&sm.out[i & (DO - 1)][k], pack_out(i, bcost, best));
     }
+}
+
+// The sweep kernel.  One lane per candidate (LPC = 1) is bounded to the
+// registers that let MIN_CTAS CTAs share an SM; the other layouts, run one
+// CTA per SM for a single pair, are left to the compiler.
+template <int C, int LPC>
+__global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS) k_sweep(const SweepArgs a) {
+    sweep_body<C, LPC>(a);
+}
+template <int C>
+__global__ void __launch_bounds__(SweepGeo<C, 1>::THREADS, SweepGeo<C, 1>::MIN_CTAS)
+    k_sweep_many(const SweepArgs a) {
+    sweep_body<C, 1>(a);
 }
 
 }  // namespace ffk

@@ -248,8 +248,9 @@ def layered_pair(seed: int = 2, width: int = 1024, height: int = 436, channels: 
                  layers: int = 4, max_disp: float = 150.0) -> FramePair:
     """Depth-ordered layers with independent affine motions (Sintel-shaped).
 
-    Layer 0 is a full-frame background; layers 1.. are star-polygon regions in
-    front of it.  Each layer's texture is multi-octave value noise plus 10-30
+    Layer 0 is a full-frame background whose motion reaches max_disp at the
+    worst frame corner; layers 1.. are star-polygon regions in front of it,
+    each with a random share (0.4..1) of the bound.  Each layer's texture is multi-octave value noise plus 10-30
     flat polygons, defined in layer coordinates and sampled analytically, so
     frame 2 is an exact re-sampling of the moved layers.  Ground truth is the
     motion of the front-most layer at each frame-1 pixel; a pixel is occluded
@@ -272,7 +273,10 @@ def layered_pair(seed: int = 2, width: int = 1024, height: int = 436, channels: 
                                        0.5 * rmax, rmax, verts=(6, 10)))
         cx = rng.uniform(0.3, 0.7) * width
         cy = rng.uniform(0.3, 0.7) * height
-        motions.append(_affine(rng, cx, cy, max_disp * rng.uniform(0.4, 1.0), width, height))
+        # the full-frame background takes the whole bound (so the far end of
+        # the displacement range occurs), the layers in front a random share
+        share = rng.uniform(0.4, 1.0)
+        motions.append(_affine(rng, cx, cy, max_disp * (1.0 if k == 0 else share), width, height))
 
     yy, xx = np.mgrid[0:height, 0:width].astype(np.float64)
 
