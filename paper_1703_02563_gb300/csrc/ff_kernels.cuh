@@ -141,6 +141,15 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// the same, under a predicate (no branch around the store)
+__device__ __forceinline__ void st_relaxed_u64_if(unsigned long long *p, unsigned long long v,
+                                                  bool pred) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %2, 0;\n\t@p st.relaxed.gpu.global.b64 [%0], %1;\n\t}"
+        ::"l"(p), "l"(v), "r"((int)pred)
+        : "memory");
+}
+
 __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

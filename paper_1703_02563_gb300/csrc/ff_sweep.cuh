@@ -538,29 +538,34 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
     const uint8_t *f2w = f2L + 4 * LWP * hw;     // this lane's words of every feature vector
     const int loy = -8 * py, hiy = 8 * (H - 1) - 8 * py;
     uint32_t last = kFlowInvalid;       // this row's sweep value at the previous step
-    int ready = 0;                      // cached in_ready
-    int ocons = 0;                      // cached out_cons
+    // The step has one branch besides the loop's: its inputs are checked at
+    // once, from values read at the end of the step before (the stager's and
+    // the random-search warp's progress, row 0's ring entry), and only a step
+    // that finds one of them short takes the slow path and reads them again.
+    // Every other condition is a select or a predicate (each branch on this
+    // chain cost about 2% of the sweep, measured).
+    int ready = 0;                      // in_ready as read at the end of the step before
+    int ocons = 0;                      // out_cons as read at the end of the step before
+    unsigned long long te_next = lds64(&sm.lring[0]);
     for (int i = 0; i < NS; i++) {
         const int u = i - k;
         const bool active = row_ok && u >= 0 && u < U;
         const int uc = min(max(u, 0), U - 1);
         const int gx = flipx ? U - 1 - uc : uc;
         const uint32_t above = __shfl_up_sync(FULL, last, G);
-        // staged inputs of step i, and (row 0) the vertical source of column i
+        // staged inputs of step i, (row 0) the vertical source of column i,
+        // and room in the result ring (the random-search warp took step i - DO)
         const bool need_top = top_src && i < U && k == 0;
-        unsigned long long te = 0;
-        if (ready <= i) ready = *v_in_ready;
-        bool ok = ready > i;
-        if (need_top) {
-            te = lds64(&sm.lring[i & (LRING - 1)]);
-            ok = ok && (uint32_t)(te >> 32) == (uint32_t)(i + 1);
-        }
+        unsigned long long te = te_next;
+        bool ok = ready > i && ocons > i - DO;
+        if (need_top) ok = ok && (uint32_t)(te >> 32) == (uint32_t)(i + 1);
         if (!__all_sync(FULL, ok)) {
             unsigned long long t0 = 0;
             while (true) {
                 if (wait_expired(t0, a.wait_ns, v_abort, a.err)) return;
-                if (ready <= i) ready = *v_in_ready;
-                ok = ready > i;
+                ready = *v_in_ready;
+                ocons = *v_out_cons;
+                ok = ready > i && ocons > i - DO;
                 if (need_top) {
                     te = lds64(&sm.lring[i & (LRING - 1)]);
                     ok = ok && (uint32_t)(te >> 32) == (uint32_t)(i + 1);
@@ -571,12 +576,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
         if (need_top && g == 0) *v_lcons = i + 1;
         const int islot = i & (DI - 1);
         // (a row before or past its columns holds no staged point: unset)
-        uint32_t cur = kFlowInvalid;
-        int ccost = kCostInvalid;
-        if (active) {
-            cur = ((volatile uint32_t *)sm.in_flow[islot])[k];
-            ccost = ((volatile int *)sm.in_cost[islot])[k];
-        }
+        const uint32_t sflow = ((volatile uint32_t *)sm.in_flow[islot])[k];
+        const int scost = ((volatile int *)sm.in_cost[islot])[k];
+        const uint32_t cur = active ? sflow : kFlowInvalid;
+        const int ccost = active ? scost : kCostInvalid;
         int4 nq[WPC];
 #pragma unroll
         for (int j = 0; j < WPC; j++) nq[j] = lds128v(&sm.in_nq[islot][k][LWP * hw + j]);
@@ -606,21 +609,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
             bcost = eh;
         }
         if (active) last = best;
-        // the strip's last row -> the next strip
-        if (edge_out && active && g == 0)
-            st_relaxed_u64(a.edge + (size_t)strip * U + u,
-                           ((unsigned long long)a.epoch << 32) | best);
-        // result -> random-search and warming warps (tagged slot); room for
-        // the next 8 steps is checked at once (ocons is warp-uniform)
-        if ((i & 7) == 0 && ocons <= i + 7 - DO) {
-            unsigned long long t2 = 0;
-            while (true) {
-                ocons = *v_out_cons;
-                if (__all_sync(FULL, ocons > i + 7 - DO)) break;
-                if (wait_expired(t2, a.wait_ns, v_abort, a.err)) return;
-            }
-        }
+        // the strip's last row -> the next strip (a predicated store)
+        st_relaxed_u64_if(a.edge + (size_t)strip * U + uc, ((unsigned long long)a.epoch << 32) | best,
+                          edge_out && active && g == 0);
+        // result -> random-search and warming warps (tagged slot)
         if (g == 0) sts64(&sm.out[i & (DO - 1)][k], pack_out(i, bcost, best));
+        // the next step's inputs, read now (checked at its start)
+        te_next = lds64(&sm.lring[(i + 1) & (LRING - 1)]);
+        ready = *v_in_ready;
+        ocons = *v_out_cons;
     }
 }
 
