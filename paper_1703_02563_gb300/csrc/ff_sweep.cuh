@@ -593,9 +593,19 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
         const uint32_t cH = clamp_s16x2(hflow, lo, hi);
         const TapRows t = taps_of<P>(cand == 0 ? cV : cH, gx, gy, L, half, U, V);
         int e = sad_taps<LWP, WPC>(f2w, t, nq);
+        // this candidate's cost and the other one's (eo); with two lanes per
+        // candidate, three independent shuffles instead of two in a row
+        int eo;
+        if constexpr (LPC == 2) {
+            const int x1 = __shfl_xor_sync(FULL, e, 1), x2 = __shfl_xor_sync(FULL, e, 2),
+                      x3 = __shfl_xor_sync(FULL, e, 3);
+            e += x1;
+            eo = x2 + x3;
+        } else {
 #pragma unroll
-        for (int o = 1; o < LPC; o <<= 1) e += __shfl_xor_sync(FULL, e, o);
-        const int eo = __shfl_xor_sync(FULL, e, LPC);     // the other candidate's cost
+            for (int o = 1; o < LPC; o <<= 1) e += __shfl_xor_sync(FULL, e, o);
+            eo = __shfl_xor_sync(FULL, e, LPC);
+        }
         const int ev = cand == 0 ? e : eo, eh = cand == 0 ? eo : e;
         // [current, vertical, horizontal]: lowest cost, the later one on ties
         uint32_t best = cur;
