@@ -525,7 +525,7 @@ namespace {
 constexpr int kMaxIters = 64;
 constexpr int kNumDirs = 3;   // forward, backward, second backward
 constexpr int kMaxChunks = 64;
-constexpr int kTargetCtas = 8 * 152;
+constexpr int kCtasPerSm = 8;     // seeding grids: about this many CTAs per SM
 constexpr int kSeedQpt = 2;
 constexpr int kSeedSample = 16;   // candidate subsampling of the bound pass
 constexpr int kSeedQueriesPerCta = 128 * kSeedQpt;
@@ -551,6 +551,7 @@ struct DirState {
 struct ff_ctx {
     ff_config cfg;
     int device = 0;
+    int sms = 152;                // SMs of the device (grid sizes of the seeding)
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr, side2 = nullptr;   // backward flows 1 and 2
     cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
@@ -746,10 +747,10 @@ ff_status validate_config(const ff_config *c, std::string *why) {
 }
 
 // seeding launch geometry: queries in tiles of 128, candidates split so the
-// grid holds about kTargetCtas CTAs
-void seed_geometry(int nq, int ncand, int *nchunks, int *chunk) {
+// grid holds about kCtasPerSm CTAs per SM of the device (sms)
+void seed_geometry(int nq, int ncand, int sms, int *nchunks, int *chunk) {
     const int qt = (nq + kSeedQueriesPerCta - 1) / kSeedQueriesPerCta;
-    int nc = (kTargetCtas + qt - 1) / qt;
+    int nc = (kCtasPerSm * sms + qt - 1) / qt;
     nc = nc < 1 ? 1 : (nc > kMaxChunks ? kMaxChunks : nc);
     int ch = (ncand + nc - 1) / nc;
     if (ch < 512) ch = 512;
@@ -757,12 +758,12 @@ void seed_geometry(int nq, int ncand, int *nchunks, int *chunk) {
     *nchunks = (ncand + ch - 1) / ch;
 }
 
-// seeding geometry of the tensor-core scan: 128 queries per CTA, candidates
-// split into chunks (whole 64-candidate tiles) so the grid holds about
-// kTargetCtas CTAs
-void seed_geometry_mma(int nq, int ncand, int *nchunks, int *chunk) {
+// seeding geometry of the mma.sync scan: 64 queries per CTA, candidates
+// split into chunks (whole 64-candidate tiles) so the grid holds about four
+// CTAs per SM of the device (sms): long chunks, few restarts
+void seed_geometry_mma(int nq, int ncand, int sms, int *nchunks, int *chunk) {
     const int qt = (nq + 63) / 64;
-    int nc = (4 * 152 + qt - 1) / qt;   // about four CTAs per SM: long chunks, few restarts
+    int nc = (4 * sms + qt - 1) / qt;
     nc = nc < 1 ? 1 : (nc > kMaxChunks ? kMaxChunks : nc);
     int ch = (ncand + nc - 1) / nc;
     ch = ((ch + 63) / 64) * 64;
@@ -803,7 +804,7 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
     // chunk of the sample bounds the query's final 8th key from above
     const int ns = (ncand + kSeedSample - 1) / kSeedSample;
     int nchunks1, chunk1;
-    seed_geometry_mma(nq, ns, &nchunks1, &chunk1);
+    seed_geometry_mma(nq, ns, c->sms, &nchunks1, &chunk1);
     {
         dim3 grid1((nq + 63) / 64, nchunks1);
         prof_begin(c, "k_seed_scan");
@@ -843,7 +844,7 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
         if ((s = check_launch(c, "k_seed_prep"))) return s;
         // one wave of two CTAs per SM (tensor memory holds two): split the
         // candidates into 128-aligned chunks
-        int nc = (2 * 152) / nq_t;
+        int nc = (2 * c->sms) / nq_t;
         nc = nc < 1 ? 1 : (nc > kMaxChunks / 2 ? kMaxChunks / 2 : nc);
         chunk = (ncand + nc - 1) / nc;
         chunk = (chunk + kTcRows - 1) / kTcRows * kTcRows;
@@ -860,7 +861,7 @@ ff_status launch_seed_knn(ff_ctx *c, int d, const uint8_t *fs, const uint8_t *fd
         if ((s = check_launch(c, "k_seed_scan"))) return s;
         nchunks *= 2;   // two lists per chunk
     } else {
-        seed_geometry_mma(nq, ncand, &nchunks, &chunk);
+        seed_geometry_mma(nq, ncand, c->sms, &nchunks, &chunk);
         dim3 grid((nq + 63) / 64, nchunks);
         prof_begin(c, "k_seed_scan");
         if (c->C == 1)
@@ -1303,6 +1304,11 @@ ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx 
     ff_ctx *c = new ff_ctx();
     c->cfg = *cfg;
     c->device = device;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return FF_ECUDA;
+    }
     c->stream = (cudaStream_t)cuda_stream;
     c->C = cfg->channels;
     c->P = cfg->channels == 1 ? 16 : 32;
@@ -1647,8 +1653,10 @@ ff_status ff_seed_knn_static(const int8_t *feat_src0, const int8_t *feat_dst0, i
     const int N = 1 << (scales - 1);
     const int Wc = (w + stride - 1) / stride, Hc = (h + stride - 1) / stride;
     const int ncand = Wc * Hc;
-    int nchunks, chunk;
-    seed_geometry((int)nq, ncand, &nchunks, &chunk);
+    int nchunks, chunk, sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return *msg = "device query failed", FF_ECUDA;
+    seed_geometry((int)nq, ncand, sms, &nchunks, &chunk);
     const int cap = (int)(max_slots / nq);
     if (nchunks > cap) {
         chunk = (ncand + cap - 1) / cap;
