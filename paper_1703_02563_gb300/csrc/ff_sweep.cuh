@@ -68,7 +68,10 @@ template <int C, int LPC> struct SweepGeo {
 
 template <int C, int LPC> struct SweepShared {
     using SG = SweepGeo<C, LPC>;
-    int4 in_nq[SG::DI][SG::RW][SG::NW];           // -64 x query, per word (4 dimensions)
+    // -64 x query, per word (4 dimensions).  The batch layout's rows are
+    // padded by one word so that its 16 rows' loads spread over the banks
+    // (6.7% faster on the Sintel-shaped pair; neutral for the one-pair layouts)
+    int4 in_nq[SG::DI][SG::RW][SG::NW + (LPC == 1 ? 1 : 0)];
     uint8_t in_raw[SG::DI][SG::RW][SG::P];        // query bytes as copied
     uint32_t in_flow[SG::DI][SG::RW];
     int in_cost[SG::DI][SG::RW];
