@@ -496,15 +496,28 @@ def run_batched(pairs, prm, slots: int, steps: int, warmup: int, local_rank: int
             **({"autotune": tuned} if tuned else {})}
 
 
+def code_hash(paths: list[str]) -> str:
+    """SHA-256 of C/CUDA sources with comments removed and whitespace runs
+    collapsed (string literals kept as they are): a change to the code changes
+    it, a change to a comment does not."""
+    import hashlib
+    import re
+    tok = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
+    parts = []
+    for p in paths:
+        text = open(os.path.join(ROOT, p), encoding="utf-8").read()
+        text = tok.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
+        parts.append(" ".join(text.split()))
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()
+
+
 def recorded_counters(kernel: str, workload: str) -> dict | None:
     """Per-launch counters of a kernel from the committed ncu summary, if they
-    were taken on this workload and the kernel's sources are unchanged since."""
-    import hashlib
+    were taken on this workload and the kernel's code is unchanged since."""
     try:
         with open(os.path.join(ROOT, "profiles", f"{kernel}_counters.json")) as f:
             rec = json.load(f)
-        src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["sources"])
-        if hashlib.sha256(src).hexdigest() != rec["source_sha256"] or rec["workload"] != workload:
+        if code_hash(rec["sources"]) != rec["code_sha256"] or rec["workload"] != workload:
             return None
         return rec
     except (OSError, KeyError, ValueError):

@@ -239,7 +239,8 @@ __device__ __forceinline__ bool wait_expired(unsigned long long &t0, unsigned lo
 //    candidates are always evaluated: a candidate equal to the current flow
 //    has exactly the cached cost, so this changes no result.  The decision
 //    goes into a tagged result slot and, for the strip's last row, into the
-//    boundary row in global memory.
+//    boundary row in global memory.  The step's inputs are read at the end
+//    of the step before and checked at once (one branch per step).
 //  * Stager warp: copies each point's pre-sweep flow, cost and query bytes
 //    into a shared ring A steps ahead (cp.async) and turns the query into
 //    -64 q per dimension, the accumulator seed of the cost's dot products.
@@ -249,7 +250,8 @@ __device__ __forceinline__ bool wait_expired(unsigned long long &t0, unsigned lo
 //    and cost.  Neighbours in this sweep see only the sweep value.
 //  * Warming warp: follows the result slots and pulls into L1 the feature
 //    sectors around each decided flow's target two points further on, where
-//    the row's next loads most likely fall.
+//    the row's next loads most likely fall (for Lab frames also those of the
+//    staged pre-sweep flows a few steps ahead).
 //  * Loader warp: copies the previous strip's boundary row into the ring.
 // Strips are handed out by a ticket counter, so a strip only waits on a
 // strip that is already running.  Every wait is bounded and warp-uniform: a

@@ -68,3 +68,18 @@ def test_sweep_roofline_arithmetic():
     assert cp["cycles_per_step"] == pytest.approx(20.0e-3 * 2000e6 / diags)
     assert cp["floor_cycles"] == pytest.approx(3 * 20 + 40 + 2 * 5 + 6 + 24 * 4)
     assert cp["frac"] == pytest.approx(cp["floor_cycles"] / cp["cycles_per_step"])
+
+
+def test_code_hash_ignores_comments_not_code(tmp_path, monkeypatch):
+    # the recorded ncu counters stay valid across comment edits only
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "a.cuh").write_text('int f(int x) {  // add one\n    return x + 1; /* done */\n}\n'
+                                    'const char *s = "// kept";\n')
+    h0 = bench.code_hash(["a.cuh"])
+    (tmp_path / "a.cuh").write_text('// a new header comment\nint f(int x) {\n  return x + 1;\n}\n'
+                                    'const char *s = "// kept";\n')
+    assert bench.code_hash(["a.cuh"]) == h0
+    (tmp_path / "a.cuh").write_text('int f(int x) {\n  return x + 2;\n}\nconst char *s = "// kept";\n')
+    assert bench.code_hash(["a.cuh"]) != h0
+    (tmp_path / "a.cuh").write_text('int f(int x) {\n  return x + 1;\n}\nconst char *s = "// gone";\n')
+    assert bench.code_hash(["a.cuh"]) != h0
