@@ -293,7 +293,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     sampler.start()
     time.sleep(0.3)
     launches0 = ff.ff_launch_count(ctx)
-    ff.ff_profile(ctx, True)
+    # the dominant kernel is timed live: one event pair per run of a level's
+    # sweeps (per-launch events would cost ~2% of the step)
+    ff.ff_profile(ctx, ff.FF_PROFILE_SWEEP_RUNS)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -307,11 +309,24 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     if world > 1:
         torch.distributed.barrier()
     ff.ff_sync(ctx)
-    ff.ff_profile(ctx, False)
+    ff.ff_profile(ctx, 0)
     launches = ff.ff_launch_count(ctx) - launches0
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
+    sweep_live = ff.ff_kernel_stats(ctx, "k_sweep")
+    # the last timed step's forward flow and mask (for `accuracy`)
+    timed_flow, timed_mask = flow_f.cpu().numpy(), mask.cpu().numpy()
+    # every kernel's launches timed one by one, over as many steps again right
+    # after the timed region: the shares and kernels_ms
+    ff.ff_profile(ctx, ff.FF_PROFILE_LAUNCHES)
+    for i in range(args.steps):
+        with torch.cuda.stream(main):
+            flush.fill_(i & 0xff)
+        step(replica_pair_id(rank, args.warmup + args.steps + i))
+    torch.cuda.synchronize()
+    ff.ff_sync(ctx)
+    ff.ff_profile(ctx, 0)
     kstats = {k: ff.ff_kernel_stats(ctx, k) for k in ff.KERNELS}
 
     # ---- end to end from pinned host buffers: ff_pair_host (one backward
@@ -349,9 +364,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     e2e_s = time.perf_counter() - t0
     n_out = 3 if args.two_way else 2
     e2e_bytes = (2 * C * W * H, n_out * 4 * WL * HL + WL * HL)
-    accuracy = flow_accuracy(flow_f.cpu().numpy(), mask.cpu().numpy(), pair, cfg.final_level())
+    accuracy = flow_accuracy(timed_flow, timed_mask, pair, cfg.final_level())
     ff.ff_destroy(ctx)
-    return {"total_ms": total_ms, "step_ms": step_ms, "kstats": kstats, "launches": launches,
+    return {"total_ms": total_ms, "step_ms": step_ms, "kstats": kstats, "sweep_live": sweep_live,
+            "launches": launches,
             "peaks": peaks,
             "accuracy": accuracy,
             "clocks": clocks, "e2e_s": e2e_s, "e2e_bytes": e2e_bytes, "W": W, "H": H, "C": C,
@@ -548,6 +564,13 @@ def roofline(res: dict, steps: int, n_dirs: int) -> dict:
     n_launch, ms = ks[dom]
     W, H, C, S, I = res["W"], res["H"], res["C"], res["S"], res["I"]
     share = ms / sum(tot.values())
+    timing = "per-launch events in a profiled pass of the same steps after the timed region"
+    if dom == "k_sweep" and res.get("sweep_live") and res["sweep_live"][0]:
+        # live: CUDA events over the timed region, one pair per run of
+        # consecutive sweeps on a stream (the run includes its launch gaps)
+        n_launch, ms = res["sweep_live"]
+        timing = ("CUDA events over the timed region on the launching streams, one pair per run "
+                  "of a level's sweeps (launch gaps inside a run included)")
     avg_ms = ms / max(n_launch, 1)
     if dom == "k_sweep":
         dims = n_dirs * steps * sweep_evals(W, H, res["cfg"]) * 9 * C / max(n_launch, 1)
@@ -571,7 +594,9 @@ def roofline(res: dict, steps: int, n_dirs: int) -> dict:
         floor = step_floor_cycles(peaks)
         return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
-                "launches": n_launch, "avg_launch_ms": avg_ms, "share": share,
+                "launches": n_launch, "avg_launch_ms": avg_ms, "share": share, "timing": timing,
+                "share_source": "per-launch events in a profiled pass of the same steps after "
+                                "the timed region",
                 "peak_source": "measured (ff_measure_peaks): the matching error's per-dimension "
                                f"arithmetic at full occupancy, {OPS_PER_DIM} ops per dimension",
                 "dp4a_peak": dp4a_peak, "frac_of_dp4a_peak": achieved / dp4a_peak,
@@ -591,7 +616,7 @@ def roofline(res: dict, steps: int, n_dirs: int) -> dict:
         achieved = flops / (avg_ms / 1e3) / 1e12
         return {"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "launches": n_launch, "avg_launch_ms": avg_ms, "share": share,
+                "launches": n_launch, "avg_launch_ms": avg_ms, "share": share, "timing": timing,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}
     return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None,
             "unit": "Tops/s", "frac": None, "traffic": None, "launches": n_launch,

@@ -301,15 +301,22 @@ typedef enum {
 } ff_debug_key;
 ff_status ff_debug_set(ff_ctx *ctx, ff_debug_key key, long long value);
 
-/* Per-launch timing for measurement.  While enabled, every kernel launch
- * is bracketed by a pair of CUDA events on the stream it is launched on.
- * ff_profile(ctx, 1) clears the record and starts recording; ff_profile(ctx,
- * 0) stops.  ff_kernel_stats (call after ff_sync) returns, for the kernel
- * named `kernel` ("k_features", "k_seed_prep", "k_seed_scan", "k_seed_merge",
- * "k_seed_rerank", "k_seed_given", "k_upsample", "k_sweep", "k_export",
- * "k_filter", "k_dense", "k_region", "k_sparsify"), the number of recorded
- * launches and their summed device time in milliseconds. */
-ff_status ff_profile(ff_ctx *ctx, int enable);
+/* Launch timing for measurement, with CUDA events on the stream each kernel
+ * is launched on.  FF_PROFILE_LAUNCHES brackets every kernel launch with an
+ * event pair.  FF_PROFILE_SWEEP_RUNS records only the sweep kernel, with one
+ * pair around each run of consecutive sweep launches on a stream (a level's
+ * sweeps), so that timing the dominant kernel adds a few events per match
+ * instead of two per launch (per-launch events cost about 2% of a pair's
+ * time); a run's time includes the launch gaps inside it.  ff_profile(ctx,
+ * mode) clears the record and starts recording; ff_profile(ctx, 0) stops (an
+ * open run ends there).  Any other mode: FF_EINVAL.  ff_kernel_stats (call
+ * after ff_sync) returns, for the kernel named `kernel` ("k_features",
+ * "k_seed_prep", "k_seed_scan", "k_seed_merge", "k_seed_rerank",
+ * "k_seed_given", "k_upsample", "k_sweep", "k_export", "k_filter", "k_dense",
+ * "k_region", "k_sparsify"), the number of recorded launches and their summed
+ * device time in milliseconds. */
+typedef enum { FF_PROFILE_LAUNCHES = 1, FF_PROFILE_SWEEP_RUNS = 2 } ff_profile_mode;
+ff_status ff_profile(ff_ctx *ctx, int mode);
 ff_status ff_kernel_stats(ff_ctx *ctx, const char *kernel, long long *launches,
                           double *total_ms);
 

@@ -577,12 +577,25 @@ struct ff_ctx {
     int force_timeout = 0;
     long long launches = 0;
     std::string last_error;
-    // per-launch timing (ff_profile): event pairs recorded on the launch stream
-    bool profiling = false;
+    // launch timing (ff_profile): event pairs recorded on the launch stream,
+    // one per launch (FF_PROFILE_LAUNCHES) or one per run of consecutive
+    // sweep launches on a stream (FF_PROFILE_SWEEP_RUNS)
+    int prof_mode = 0;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    std::vector<int> prof_kernel;
+    struct ProfRec {
+        int kernel, launches;
+        size_t ev0, ev1;   // indices into ev_pool
+    };
+    std::vector<ProfRec> prof;
     const char *pending_kernel = nullptr;
+    size_t pending_ev = 0;
+    struct SweepRun {
+        cudaStream_t stream;
+        size_t ev0;
+        int launches;
+    };
+    std::vector<SweepRun> runs;   // open runs, at most one per stream
 };
 
 namespace {
@@ -629,25 +642,64 @@ cudaEvent_t pool_event(ff_ctx *c) {
     return c->ev_pool[c->ev_used++];
 }
 
-// brackets the next launch with an event pair when profiling is on
+// ends open sweep run r: its end event on its own stream, one record
+void close_run(ff_ctx *c, size_t r) {
+    const ff_ctx::SweepRun run = c->runs[r];
+    c->runs.erase(c->runs.begin() + (long)r);
+    cudaEvent_t e = pool_event(c);
+    if (!e) return;   // (the run is dropped)
+    cudaEventRecord(e, run.stream);
+    c->prof.push_back({kernel_id("k_sweep"), run.launches, run.ev0, c->ev_used - 1});
+}
+
+// Called before each launch while profiling.  Per launch: the start event.
+// Sweep runs: a sweep launch opens a run on its stream (or extends the open
+// one); any other launch on that stream closes it first.
 void prof_begin(ff_ctx *c, const char *kernel) {
-    if (!c->profiling) return;
+    if (c->prof_mode == 0) return;
+    if (c->prof_mode == FF_PROFILE_SWEEP_RUNS) {
+        const bool sweep = strcmp(kernel, "k_sweep") == 0;
+        for (size_t r = 0; r < c->runs.size(); r++) {
+            if (c->runs[r].stream != c->stream) continue;
+            if (sweep) {
+                c->pending_kernel = kernel;
+                return;
+            }
+            close_run(c, r);
+            break;
+        }
+        if (!sweep) return;
+        cudaEvent_t e = pool_event(c);
+        if (!e) return;
+        cudaEventRecord(e, c->stream);
+        c->runs.push_back({c->stream, c->ev_used - 1, 0});
+        c->pending_kernel = kernel;
+        return;
+    }
     cudaEvent_t e = pool_event(c);
     if (!e) return;
     cudaEventRecord(e, c->stream);
     c->pending_kernel = kernel;
+    c->pending_ev = c->ev_used - 1;
 }
 
 ff_status check_launch(ff_ctx *ctx, const char *what) {
     ctx->launches++;
     const ff_status s = check_cuda(ctx, cudaGetLastError(), what);
-    if (ctx->profiling && ctx->pending_kernel) {
-        cudaEvent_t e = pool_event(ctx);
-        if (e) {
-            cudaEventRecord(e, ctx->stream);
-            ctx->prof_kernel.push_back(kernel_id(ctx->pending_kernel));
+    if (ctx->prof_mode != 0 && ctx->pending_kernel) {
+        if (ctx->prof_mode == FF_PROFILE_SWEEP_RUNS) {
+            for (auto &r : ctx->runs)
+                if (r.stream == ctx->stream) {
+                    r.launches++;
+                    break;
+                }
         } else {
-            ctx->ev_used--;   // drop the unmatched start event
+            cudaEvent_t e = pool_event(ctx);
+            if (e) {
+                cudaEventRecord(e, ctx->stream);
+                ctx->prof.push_back(
+                    {kernel_id(ctx->pending_kernel), 1, ctx->pending_ev, ctx->ev_used - 1});
+            }
         }
         ctx->pending_kernel = nullptr;
     }
@@ -1801,13 +1853,18 @@ ff_status ff_debug_set(ff_ctx *c, ff_debug_key key, long long value) {
     return fail(c, FF_EINVAL, "unknown debug key");
 }
 
-ff_status ff_profile(ff_ctx *c, int enable) {
+ff_status ff_profile(ff_ctx *c, int mode) {
     if (!c) return FF_EINVAL;
-    if (enable) {
+    if (mode != 0 && mode != FF_PROFILE_LAUNCHES && mode != FF_PROFILE_SWEEP_RUNS)
+        return fail(c, FF_EINVAL, "profile mode must be 0, FF_PROFILE_LAUNCHES or "
+                                  "FF_PROFILE_SWEEP_RUNS");
+    DeviceGuard guard(c->device);
+    while (!c->runs.empty()) close_run(c, 0);   // runs still open end here
+    if (mode != 0) {
         c->ev_used = 0;
-        c->prof_kernel.clear();
+        c->prof.clear();
     }
-    c->profiling = enable != 0;
+    c->prof_mode = mode;
     c->pending_kernel = nullptr;
     return FF_OK;
 }
@@ -1819,12 +1876,12 @@ ff_status ff_kernel_stats(ff_ctx *c, const char *kernel, long long *launches, do
     DeviceGuard guard(c->device);
     long long n = 0;
     double ms = 0.0;
-    for (size_t k = 0; k < c->prof_kernel.size(); k++) {
-        if (c->prof_kernel[k] != id) continue;
+    for (const auto &r : c->prof) {
+        if (r.kernel != id) continue;
         float t = 0.f;
-        const cudaError_t e = cudaEventElapsedTime(&t, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]);
+        const cudaError_t e = cudaEventElapsedTime(&t, c->ev_pool[r.ev0], c->ev_pool[r.ev1]);
         if (e != cudaSuccess) return check_cuda(c, e, "cudaEventElapsedTime");
-        n++;
+        n += r.launches;
         ms += t;
     }
     *launches = n;

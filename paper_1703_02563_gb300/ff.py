@@ -20,6 +20,7 @@ FF_FWD, FF_BWD, FF_BWD2 = 0, 1, 2
 FF_SCHED_BASIC, FF_SCHED_PLUS, FF_SCHED_PLUS_FAST, FF_SCHED_PLUS_FAST_X2 = 0, 1, 2, 3
 FF_DEBUG_WAIT_LIMIT_NS, FF_DEBUG_FORCE_TIMEOUT, FF_DEBUG_SWEEP_LANES = 1, 2, 4
 FF_DEBUG_SEED_TC = 5
+FF_PROFILE_LAUNCHES, FF_PROFILE_SWEEP_RUNS = 1, 2
 INVALID = -32768
 
 EXPORTED = ("ff_config_default", "ff_create", "ff_set_stream", "ff_features", "ff_match",
@@ -333,12 +334,14 @@ def ff_measure_peaks(device: int = 0) -> dict:
     return {name: getattr(out, name) for name, _ in ff_peaks._fields_}
 
 
-def ff_profile(ctx: int, enable: bool) -> None:
-    _check(ctx, lib().ff_profile(ctx, 1 if enable else 0))
+def ff_profile(ctx: int, mode: int) -> None:
+    """0 stops; FF_PROFILE_LAUNCHES (or True) times every launch;
+    FF_PROFILE_SWEEP_RUNS times each run of consecutive sweep launches."""
+    _check(ctx, lib().ff_profile(ctx, int(mode)))
 
 
 def ff_kernel_stats(ctx: int, kernel: str) -> tuple[int, float]:
-    """(launches, summed device ms) of `kernel` recorded since ff_profile(ctx, 1)."""
+    """(launches, summed device ms) of `kernel` recorded since ff_profile started."""
     n = ct.c_longlong(0)
     ms = ct.c_double(0.0)
     _check(ctx, lib().ff_kernel_stats(ctx, kernel.encode(), ct.byref(n), ct.byref(ms)))

@@ -327,6 +327,33 @@ def test_full_size_end_to_end(name):
     ctx.close()
 
 
+def test_profile_modes_record_the_same_sweeps():
+    # per-launch timing and per-run timing of the sweeps count the same sweep
+    # launches; the run mode records nothing else; flows are unchanged by either
+    pair, prm = workloads.make_workload("tiny128x96")
+    S, I = prm["scales"], prm["iters"]
+    ctx = _ctx(1, S, I, pair.width, pair.height)
+    _load(ctx, pair)
+    ref = _host(ctx.match(ff.FF_FWD, 5)[0])
+    got = {}
+    for mode in (ff.FF_PROFILE_LAUNCHES, ff.FF_PROFILE_SWEEP_RUNS):
+        ff.ff_profile(ctx.ctx, mode)
+        f = ctx.match(ff.FF_FWD, 5)[0]
+        ctx.match(ff.FF_BWD, 5)
+        ctx.sync()
+        ff.ff_profile(ctx.ctx, 0)
+        np.testing.assert_array_equal(_host(f), ref)
+        got[mode] = {k: ff.ff_kernel_stats(ctx.ctx, k) for k in ff.KERNELS}
+    per_launch, runs = got[ff.FF_PROFILE_LAUNCHES], got[ff.FF_PROFILE_SWEEP_RUNS]
+    sweeps = 2 * sum(ff.Config(channels=1, scales=S, iters=I).sweeps(L) for L in range(S))
+    assert per_launch["k_sweep"][0] == runs["k_sweep"][0] == sweeps
+    assert runs["k_sweep"][1] > 0 and per_launch["k_upsample"][0] > 0
+    assert all(n == 0 for k, (n, _) in runs.items() if k != "k_sweep")
+    with pytest.raises(ff.FFError):
+        ff.ff_profile(ctx.ctx, 3)
+    ctx.close()
+
+
 def test_deterministic_and_concurrent_streams_agree():
     torch = _torch()
     pair = workloads.layered_pair(seed=21, width=160, height=120, channels=3, max_disp=30)
