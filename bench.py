@@ -253,19 +253,27 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict:
     ev_fork = torch.cuda.Event()
     ev_join = torch.cuda.Event()
     ev_join2 = torch.cuda.Event()
+    ev_feat = torch.cuda.Event()
 
     def step(pair_id: int, i1=img1, i2=img2):
-        # features on the main stream; the backward flow(s) on side streams
+        # the two frames' features on the main and side streams (each stream
+        # then waits for the other's); the backward flow(s) on side streams
         # overlap the forward flow; the filter joins them
-        ff.ff_set_stream(ctx, main)
-        ff.ff_features(ctx, 0, i1, W, H, W)
-        ff.ff_features(ctx, 1, i2, W, H, W)
         ev_fork.record(main)
         side.wait_event(ev_fork)
+        ff.ff_set_stream(ctx, main)
+        ff.ff_features(ctx, 0, i1, W, H, W)
+        ff.ff_set_stream(ctx, side)
+        ff.ff_features(ctx, 1, i2, W, H, W)
+        ev_fork.record(main)
+        ev_feat.record(side)
+        side.wait_event(ev_fork)
+        main.wait_event(ev_feat)
         ff.ff_set_stream(ctx, side)
         ff.ff_match(ctx, ff.FF_BWD, pair_id, None, flow_b, None)
         if args.two_way:
             side2.wait_event(ev_fork)
+            side2.wait_event(ev_feat)
             ff.ff_set_stream(ctx, side2)
             ff.ff_match(ctx, ff.FF_BWD2, pair_id, None, flow_b2, None)
         ff.ff_set_stream(ctx, main)

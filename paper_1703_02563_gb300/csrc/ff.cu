@@ -28,15 +28,29 @@ using namespace ffk;
 //   DC: round(c/64) - 128, others: round(c/16), both saturated.
 // One thread per level pixel; a 16x16 tile plus its 7-pixel halo of D_n is
 // built in shared memory straight from the frame, then the coefficients come
-// from separable +-1 row and column sums.
+// from separable +-1 row and column sums.  One launch covers every level of
+// a frame (the levels are independent: each is computed from the frame), its
+// blocks listed coarsest level first, since a coarse tile sums the most frame
+// pixels per level pixel.
+struct FeatLevels {
+    int n;                                    // levels in this launch
+    int L[FF_MAX_SCALES], WL[FF_MAX_SCALES], HL[FF_MAX_SCALES];
+    int tiles_x[FF_MAX_SCALES];               // 16-pixel tiles across the level
+    int first[FF_MAX_SCALES + 1];             // first block of each level
+    uint8_t *out[FF_MAX_SCALES];
+};
 template <int C>
 __global__ void __launch_bounds__(256)
-    k_features(const uint8_t *__restrict__ img, int pitch, int W, int H, int L, int WL, int HL,
-               uint8_t *__restrict__ out) {
+    k_features(const uint8_t *__restrict__ img, int pitch, int W, int H, const FeatLevels lv) {
     constexpr int TS = 16, TW = TS + 7, P = Geo<C>::P;
     __shared__ int16_t sD[C][TW][TW];
+    int li = 0;
+    while (li + 1 < lv.n && (int)blockIdx.x >= lv.first[li + 1]) li++;
+    const int b = (int)blockIdx.x - lv.first[li];
+    const int L = lv.L[li], WL = lv.WL[li], HL = lv.HL[li];
+    uint8_t *__restrict__ out = lv.out[li];
     const int n = 1 << L;
-    const int bx = blockIdx.x * TS, by = blockIdx.y * TS;
+    const int bx = (b % lv.tiles_x[li]) * TS, by = (b / lv.tiles_x[li]) * TS;
     const int tid = threadIdx.y * TS + threadIdx.x;
     const int half = (n * n) >> 1;
     for (int k = tid; k < C * TW * TW; k += TS * TS) {
@@ -1136,16 +1150,26 @@ ff_status enqueue_pair(ff_ctx *c, const uint8_t *img1, const uint8_t *img2, int 
     const int n = level_sweeps(c->cfg, Lf);
     cudaStream_t main = c->stream;
     ff_status s;
-    if ((s = ff_features(c, 0, img1, w, h, pitch))) return s;
-    if ((s = ff_features(c, 1, img2, w, h, pitch))) return s;
+    // the two frames' features on the two streams (the side stream starts
+    // after what main holds so far), then each stream waits for the other's
     if ((s = check_cuda(c, cudaEventRecord(c->ev_a, main), "event"))) return s;
     if ((s = check_cuda(c, cudaStreamWaitEvent(c->side, c->ev_a, 0), "wait"))) return s;
+    if ((s = ff_features(c, 0, img1, w, h, pitch))) return s;
+    c->stream = c->side;
+    s = ff_features(c, 1, img2, w, h, pitch);
+    c->stream = main;
+    if (s) return s;
+    if ((s = check_cuda(c, cudaEventRecord(c->ev_a, main), "event"))) return s;
+    if ((s = check_cuda(c, cudaEventRecord(c->ev_c, c->side), "event"))) return s;
+    if ((s = check_cuda(c, cudaStreamWaitEvent(c->side, c->ev_a, 0), "wait"))) return s;
+    if ((s = check_cuda(c, cudaStreamWaitEvent(main, c->ev_c, 0), "wait"))) return s;
     c->stream = c->side;
     s = run_match(c, FF_BWD, pair_id, nullptr, Lf, n, bwd, nullptr);
     c->stream = main;
     if (s) return s;
     if (bwd2) {
         if ((s = check_cuda(c, cudaStreamWaitEvent(c->side2, c->ev_a, 0), "wait"))) return s;
+        if ((s = check_cuda(c, cudaStreamWaitEvent(c->side2, c->ev_c, 0), "wait"))) return s;
         c->stream = c->side2;
         s = run_match(c, FF_BWD2, pair_id, nullptr, Lf, n, bwd2, nullptr);
         c->stream = main;
@@ -1442,24 +1466,45 @@ ff_status ff_features(ff_ctx *c, int slot, const uint8_t *img, int w, int h, int
     if (pitch < w) return fail(c, FF_EINVAL, "pitch < width");
     DeviceGuard guard(c->device);
     c->have[slot] = false;
-    for (int L = 0; L < c->S; L++) {
-        int WL, HL;
-        level_dims(w, h, L, &WL, &HL);
-        uint8_t *out = c->feat[slot] + level_offset(w, h, c->P, L);
-        dim3 grid((WL + 15) / 16, (HL + 15) / 16), block(16, 16);
-        prof_begin(c, "k_features");
-        if (c->cfg.wht_tensor_cores) {
+    if (c->cfg.wht_tensor_cores) {
+        for (int L = 0; L < c->S; L++) {
+            int WL, HL;
+            level_dims(w, h, L, &WL, &HL);
+            uint8_t *out = c->feat[slot] + level_offset(w, h, c->P, L);
+            dim3 grid((WL + 15) / 16, (HL + 15) / 16);
+            prof_begin(c, "k_features");
             if (c->C == 1)
                 k_features_tc<1, false><<<grid, 128, 0, c->stream>>>(img, pitch, w, h, L, WL, HL,
                                                                      out, nullptr);
             else
                 k_features_tc<3, false><<<grid, 128, 0, c->stream>>>(img, pitch, w, h, L, WL, HL,
                                                                      out, nullptr);
-        } else if (c->C == 1) {
-            k_features<1><<<grid, block, 0, c->stream>>>(img, pitch, w, h, L, WL, HL, out);
-        } else {
-            k_features<3><<<grid, block, 0, c->stream>>>(img, pitch, w, h, L, WL, HL, out);
+            ff_status s = check_launch(c, "k_features");
+            if (s) return s;
         }
+    } else {
+        // every level in one launch, coarsest first
+        FeatLevels lv{};
+        lv.n = c->S;
+        int blocks = 0;
+        for (int k = 0; k < c->S; k++) {
+            const int L = c->S - 1 - k;
+            int WL, HL;
+            level_dims(w, h, L, &WL, &HL);
+            lv.L[k] = L;
+            lv.WL[k] = WL;
+            lv.HL[k] = HL;
+            lv.tiles_x[k] = (WL + 15) / 16;
+            lv.first[k] = blocks;
+            lv.out[k] = c->feat[slot] + level_offset(w, h, c->P, L);
+            blocks += lv.tiles_x[k] * ((HL + 15) / 16);
+        }
+        lv.first[c->S] = blocks;
+        prof_begin(c, "k_features");
+        if (c->C == 1)
+            k_features<1><<<blocks, dim3(16, 16), 0, c->stream>>>(img, pitch, w, h, lv);
+        else
+            k_features<3><<<blocks, dim3(16, 16), 0, c->stream>>>(img, pitch, w, h, lv);
         ff_status s = check_launch(c, "k_features");
         if (s) return s;
     }
