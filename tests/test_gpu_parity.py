@@ -55,7 +55,10 @@ def _gt_seeds(pair, S):
 
 
 FEATURE_CASES = [(1, 128, 96, 3), (1, 37, 29, 4), (3, 97, 71, 3), (3, 16, 9, 2), (1, 1, 1, 1),
-                 (1, 200, 3, 3), (3, 65, 130, 4)]
+                 (1, 200, 3, 3), (3, 65, 130, 4),
+                 # one launch covers every level: up to the eight the ABI allows, down
+                 # to levels 2 px across
+                 (3, 300, 170, 8), (1, 513, 257, 6), (3, 37, 300, 7)]
 
 
 @pytest.mark.parametrize("C,W,H,S", FEATURE_CASES)
