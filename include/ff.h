@@ -109,9 +109,10 @@ ff_status ff_config_default(ff_config *cfg);
 ff_status ff_create(const ff_config *cfg, int device, void *cuda_stream, ff_ctx **out);
 
 /* Makes later calls enqueue on another stream.  Features and matching state
- * of the two slots / directions are separate buffers, so ff_match(FF_FWD)
- * and ff_match(FF_BWD) may run concurrently on two streams once both
- * frames' features are complete (ordering them is the caller's job). */
+ * of the two slots / directions are separate buffers, so ff_features of
+ * slot 0 and of slot 1 may run concurrently on two streams, and so may
+ * ff_match(FF_FWD) and ff_match(FF_BWD) once both frames' features are
+ * complete (ordering them is the caller's job). */
 ff_status ff_set_stream(ff_ctx *ctx, void *cuda_stream);
 
 /* Sec. 3.1 + 3.6: builds the S level images of one frame (n x n area
