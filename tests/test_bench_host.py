@@ -68,6 +68,15 @@ def test_sweep_roofline_arithmetic():
     assert cp["cycles_per_step"] == pytest.approx(20.0e-3 * 2000e6 / diags)
     assert cp["floor_cycles"] == pytest.approx(3 * 20 + 40 + 2 * 5 + 6 + 24 * 4)
     assert cp["frac"] == pytest.approx(cp["floor_cycles"] / cp["cycles_per_step"])
+    # the live sweep runs of the timed region (10 launches in 18 ms) take over the
+    # launch time and the critical path; the share stays the per-launch pass's
+    res["sweep_live"] = (10, 18.0)
+    r2 = bench.roofline(res, steps=1, n_dirs=1)
+    assert r2["avg_launch_ms"] == pytest.approx(1.8)
+    assert r2["achieved"] == pytest.approx(ops_per_launch / 1.8e-3 / 1e12)
+    assert r2["critical_path"]["cycles_per_step"] == pytest.approx(18.0e-3 * 2000e6 / diags)
+    assert r2["share"] == pytest.approx(20.0 / 20.5)
+    assert "timed region" in r2["timing"] and "profiled pass" in r["timing"]
 
 
 def test_code_hash_ignores_comments_not_code(tmp_path, monkeypatch):
